@@ -1,0 +1,179 @@
+/*
+ * tprobe.h -- C ABI of the GB300 (sm_103a) probed FWI-gradient library.
+ *
+ * Implements the low-memory adjoint-state gradient of Louboutin & Herrmann,
+ * "Ultra-low memory seismic inversion with randomized trace estimation"
+ * (arXiv 2104.00794): constant-density acoustic finite differences, 2nd order
+ * in time and 4th/8th order in space, whose forward and adjoint time loops
+ * accumulate the wavefields projected onto r random time probes (Algorithm 1)
+ * instead of storing the N x nt forward history (Eq. 3).
+ *
+ * Discrete system (shared reading of the paper, which gives no
+ * discretisation): nodes nz x ny x nx (ny = 1 in 2-D), spacing h, zero
+ * (Dirichlet) values outside the grid, flat index (z*ny + y)*nx + x.
+ * Levels t = 0..nt-1 with u[0] = u[1] = 0 and, for t = 1..nt-2,
+ *     u[t+1] = 2u[t] - u[t-1] + dt^2 v^2 (L u[t] + S^T q[t])
+ * (Algorithm 1 line 1, operator f; L = centred Laplacian, Fornberg weights);
+ * data d[t] = R u[t] (Eq. 2).  The adjoint (Algorithm 1 line 5, f^T) is the
+ * exact transpose: lambda[nt] = lambda[nt+1] = 0 and, for j = nt-1..2,
+ *     lambda[j] = 2 lambda[j+1] - lambda[j+2] + dt^2 v^2 (L lambda[j+1] + R^T s[j]).
+ * m = 1/v^2 is the squared slowness; every gradient returned is dJ/dm of
+ * J = 1/2 sum_t ||R u[t] - d_obs[t]||^2 (Eq. 2), i.e. the negative of the
+ * update direction delta m that Eq. 3 prints without a sign.
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers owned by the caller, unless a
+ *     parameter says "host".  Nothing is allocated on the hot path: scratch
+ *     space is the caller's workspace, sized by tp_workspace_bytes().
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t, NULL for
+ *     the legacy default stream); results are ready once the stream is.
+ *   - float = IEEE fp32; the wavefields are fp32 and the misfit / gradient
+ *     norm are fp64 reductions.
+ *   - Errors are returned as tp_status, never thrown; tp_last_error() gives a
+ *     thread-local message for the last failing call on the calling thread.
+ *   - Calls that share a workspace must not overlap on the device.
+ */
+#ifndef TPROBE_H
+#define TPROBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TP_OK = 0,
+  TP_ERR_ARG = 1,       /* invalid argument (sizes, pointers, geometry) */
+  TP_ERR_UNSTABLE = 2,  /* CFL condition of the leapfrog scheme violated */
+  TP_ERR_NOMEM = 3,     /* workspace smaller than tp_workspace_bytes() */
+  TP_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed */
+  TP_ERR_TIMEOUT = 5    /* a bounded device-side wait gave up */
+} tp_status;
+
+typedef enum {
+  TP_PROBE_RADEMACHER = 0, /* +-1 entries (Eq. 1, random sign probes) */
+  TP_PROBE_GAUSSIAN = 1,   /* Irwin-Hall(12) approximately normal entries */
+  TP_PROBE_IDENTITY = 2,   /* Z = I, r = nt: reproduces Eq. 3 exactly */
+  TP_PROBE_USER = 3        /* caller-supplied Z (e.g. QR range-finder probes) */
+} tp_probe_kind;
+
+typedef enum {
+  TP_OP_FORWARD = 0,
+  TP_OP_ADJOINT = 1,
+  TP_OP_GRADIENT_PROBED = 2,
+  TP_OP_GRADIENT_FULL = 3
+} tp_op;
+
+/* Grid and time axis.  Eq. 2 (F(m; q) on this grid). */
+typedef struct {
+  int ndim;    /* 2 or 3 */
+  int nx, ny, nz; /* nodes; ny must be 1 when ndim == 2 */
+  float h;     /* grid spacing [m] */
+  float dt;    /* time step [s] */
+  int nt;      /* number of time levels (>= 3) */
+  int order;   /* spatial order: 4 or 8 */
+  float vmax;  /* > 0: caller-asserted max velocity used for the CFL check
+                  (no device synchronisation); 0: the library reduces the
+                  velocity on the device and synchronises the stream once */
+} tp_grid;
+
+/* Acquisition of a batch of independent shots sharing one model.  S^T and R
+ * of Eq. 2 / Algorithm 1: on-grid point sources and receivers. */
+typedef struct {
+  int nshots;          /* shots in the batch (>= 1) */
+  int nsrc;            /* sources per shot (>= 1) */
+  const int64_t* src;  /* device [nshots][nsrc] flat node indices */
+  int nrec;            /* receivers per shot (>= 1) */
+  const int64_t* rec;  /* device [nshots][nrec] flat node indices */
+} tp_geom;
+
+/* Probing matrix Q in R^{nt x r} of Eq. 4 / Algorithm 1, drawn per shot. */
+typedef struct {
+  int kind;            /* tp_probe_kind */
+  int r;               /* probing vectors, 1..256 (== nt for IDENTITY) */
+  int T;               /* time window of the probe GEMM: 32 or 64 levels */
+  uint64_t seed;       /* SplitMix64 seed (random kinds) */
+  const float* Z_user; /* device [nshots][nt][r] when kind == TP_PROBE_USER */
+  float scale;         /* estimator scale; 0 selects the default: 1/r for
+                          random probes (Eq. 1), 1 for IDENTITY and USER */
+} tp_probe;
+
+/* Bytes of device workspace that `op` needs (0 on invalid arguments; see
+ * tp_last_error).  `probe` is read only for TP_OP_GRADIENT_PROBED.  The
+ * workspace must be 256-byte aligned. */
+size_t tp_workspace_bytes(int op, const tp_grid* grid, const tp_geom* geom, const tp_probe* probe);
+
+/* Forward modelling d = F(m; q) (Eq. 2; Algorithm 1 lines 0-3 without the
+ * probe accumulation).  vel: [nz][ny][nx] m/s.  wavelet: [nshots][nt][nsrc]
+ * source time functions q.  d_out: [nshots][nt][nrec], d_out[s][t] = R u[t]
+ * (levels 0 and 1 are zero). */
+tp_status tp_forward(const tp_grid* grid, const tp_geom* geom, const float* vel,
+                     const float* wavelet, float* d_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint q = F^T s (Algorithm 1 lines 4-7 without the probe accumulation).
+ * d_in: [nshots][nt][nrec] adjoint sources s.  q_out: [nshots][nt][nsrc],
+ * q_out[s][t] = S lambda[t+1] for t = 1..nt-2 and 0 for t = 0, nt-1, so that
+ * <F q, s> = <q, F^T s> holds to rounding. */
+tp_status tp_adjoint(const tp_grid* grid, const tp_geom* geom, const float* vel,
+                     const float* d_in, float* q_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Probed gradient (Algorithm 1, Eq. 4) summed over the batch's shots:
+ *   grad[x] = - scale * sum_s sum_i ubar_s[x,i] vbar_s[x,i],
+ *   ubar_s[x,i] = sum_{k=2}^{nt-1} Q_s[k,i] udd_s[k,x],  vbar likewise with lambda_s,
+ * where udd[k] = (u[k] - 2u[k-1] + u[k-2]) / dt^2 and lambda is driven by the
+ * residual d - d_obs.  grad: [nz][ny][nx] (dJ/dm).  misfit, gnorm: optional
+ * DEVICE doubles receiving J = 1/2 ||d - d_obs||^2 and ||grad||_2.
+ * d_obs: [nshots][nt][nrec].  Memory: 2 N r probe accumulators per shot plus
+ * a (T + 2)-level ring, instead of the N nt history of tp_gradient_full. */
+tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe,
+                             const float* vel, const float* wavelet, const float* d_obs,
+                             float* grad, double* misfit, double* gnorm, void* ws,
+                             size_t ws_bytes, void* stream);
+
+/* Conventional adjoint-state gradient (Eq. 3) with the full N x nt forward
+ * history kept in the workspace; same arguments and outputs as
+ * tp_gradient_probed without the probes. */
+tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float* vel,
+                           const float* wavelet, const float* d_obs, float* grad, double* misfit,
+                           double* gnorm, void* ws, size_t ws_bytes, void* stream);
+
+/* The probing matrix that tp_gradient_probed draws for shot `shot`
+ * (Eq. 1 probes from SplitMix64; Z[t][i], [nt][r], unscaled).  For
+ * TP_PROBE_USER it copies the caller's Z. */
+tp_status tp_probes(const tp_probe* probe, int nt, int shot, float* Z, void* stream);
+
+/* Synchronises `stream` and reports whether a bounded device-side wait in
+ * the last call on this workspace gave up (TP_ERR_TIMEOUT) or not (TP_OK);
+ * clears the flag. */
+tp_status tp_workspace_status(void* ws, size_t ws_bytes, void* stream);
+
+/* Thread-local message of the last error on the calling thread ("" if none). */
+const char* tp_last_error(void);
+
+/* ---- kernel timing (CUDA events around every launch, for rooflines) ---- */
+typedef enum {
+  TP_KERNEL_STENCIL = 0,  /* leapfrog step, forward or adjoint (K1/K2) */
+  TP_KERNEL_IMAGING = 1,  /* stencil-form imaging / probe combine sweep */
+  TP_KERNEL_PROBE_GEMM = 2, /* windowed probe GEMM on tcgen05 (K3) */
+  TP_KERNEL_POINT = 3,    /* source injection + receiver sampling */
+  TP_KERNEL_REDUCE = 4,   /* residual, misfit and norm reductions */
+  TP_KERNEL_OTHER = 5,    /* setup kernels, probe generation, finish */
+  TP_KERNEL_KINDS = 6
+} tp_kernel_kind;
+
+/* Starts recording a CUDA event pair around every kernel launch of the
+ * calling process (at most `max_launches` pairs; 0 = 65536). */
+tp_status tp_profile_begin(int max_launches);
+/* Stops recording, synchronises and writes per kind the summed duration in
+ * ms and the number of launches (host arrays of TP_KERNEL_KINDS entries). */
+tp_status tp_profile_end(double* ms, int64_t* launches);
+/* Name of a tp_kernel_kind. */
+const char* tp_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPROBE_H */

@@ -1,0 +1,177 @@
+"""Torch-facing helpers over the C ABI (device memory and streams only).
+
+``Problem`` holds one batch of shots on the device (grid, geometry) and
+allocates the caller-owned workspace with torch; every computation is a call
+into libtprobe through ``native``.  Tensors passed in must be contiguous
+float32 CUDA tensors of the documented shapes.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import torch
+
+from . import native
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _f32(t, device) -> torch.Tensor:
+    t = torch.as_tensor(t, device=device)
+    if t.dtype != torch.float32:
+        t = t.to(torch.float32)
+    return t.contiguous()
+
+
+@dataclasses.dataclass
+class ProbeSpec:
+    kind: str = "rademacher"
+    r: int = 4
+    T: int = 32
+    seed: int = 2104
+    scale: float = 0.0
+    Z_user: Optional[torch.Tensor] = None
+
+    def to_c(self) -> native.tp_probe:
+        return native.tp_probe(native.PROBE_KINDS[self.kind], int(self.r), int(self.T), int(self.seed) & (2**64 - 1),
+                               _ptr(self.Z_user) if self.Z_user is not None else None, float(self.scale))
+
+
+class Problem:
+    """A batch of shots on one model grid, with device-resident geometry."""
+
+    def __init__(self, ndim, nx, ny, nz, h, dt, nt, order, src, rec, vmax: float = 0.0, device="cuda"):
+        self.device = torch.device(device)
+        self.src = torch.as_tensor(src, dtype=torch.int64, device=self.device).contiguous()
+        self.rec = torch.as_tensor(rec, dtype=torch.int64, device=self.device).contiguous()
+        if self.src.dim() == 1:
+            self.src = self.src[None]
+        if self.rec.dim() == 1:
+            self.rec = self.rec[None]
+        self.nshots = int(self.src.shape[0])
+        if self.rec.shape[0] != self.nshots:
+            raise ValueError("src and rec need the same number of shots")
+        self.grid = native.tp_grid(int(ndim), int(nx), int(ny), int(nz), float(h), float(dt), int(nt), int(order),
+                                   float(vmax))
+        self.geom = native.tp_geom(self.nshots, int(self.src.shape[1]), self.src.data_ptr(),
+                                   int(self.rec.shape[1]), self.rec.data_ptr())
+        self._ws = {}
+
+    @classmethod
+    def from_workload(cls, w, nt=None, vmax=None, device="cuda"):
+        vm = float(max(w.vel_true.max(), w.vel0.max())) if vmax is None else vmax
+        return cls(w.ndim, w.nx, w.ny, w.nz, w.h, w.dt, w.nt if nt is None else nt, w.order, w.src, w.rec,
+                   vmax=vm, device=device)
+
+    # ---------------------------------------------------------------- sizes
+    @property
+    def nt(self):
+        return self.grid.nt
+
+    @property
+    def N(self):
+        return self.grid.nx * self.grid.ny * self.grid.nz
+
+    @property
+    def shape(self):
+        g = self.grid
+        return (g.nz, g.ny, g.nx) if g.ndim == 3 else (g.nz, g.nx)
+
+    def workspace_bytes(self, op: int, probe: Optional[ProbeSpec] = None) -> int:
+        return native.tp_workspace_bytes(op, self.grid, self.geom, probe.to_c() if probe is not None else None)
+
+    def workspace(self, op: int, probe: Optional[ProbeSpec] = None) -> tuple[int, int]:
+        """(pointer, bytes) of a cached, 256-byte aligned workspace for `op`."""
+        n = self.workspace_bytes(op, probe)
+        buf = self._ws.get(op)
+        if buf is None or buf.numel() < n + 256:
+            self._ws.pop(op, None)
+            buf = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+            self._ws[op] = buf
+        p = buf.data_ptr()
+        p += (-p) % 256
+        return p, n
+
+    def release(self):
+        self._ws.clear()
+
+    # ---------------------------------------------------------------- operators
+    def forward(self, vel, wavelet, d_out=None):
+        vel, wavelet = _f32(vel, self.device), _f32(wavelet, self.device)
+        if d_out is None:
+            d_out = torch.empty((self.nshots, self.nt, self.geom.nrec), dtype=torch.float32, device=self.device)
+        ws, n = self.workspace(native.OP_FORWARD)
+        native.tp_forward(self.grid, self.geom, _ptr(vel), _ptr(wavelet), _ptr(d_out), ws, n, _stream())
+        return d_out
+
+    def adjoint(self, vel, d_in, q_out=None):
+        vel, d_in = _f32(vel, self.device), _f32(d_in, self.device)
+        if q_out is None:
+            q_out = torch.empty((self.nshots, self.nt, self.geom.nsrc), dtype=torch.float32, device=self.device)
+        ws, n = self.workspace(native.OP_ADJOINT)
+        native.tp_adjoint(self.grid, self.geom, _ptr(vel), _ptr(d_in), _ptr(q_out), ws, n, _stream())
+        return q_out
+
+    def gradient_probed(self, vel, wavelet, d_obs, probe: ProbeSpec, grad=None, scalars=None):
+        """(grad [dJ/dm], scalars[2] = (misfit, ||grad||)) as device tensors."""
+        vel, wavelet, d_obs = _f32(vel, self.device), _f32(wavelet, self.device), _f32(d_obs, self.device)
+        if grad is None:
+            grad = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        if scalars is None:
+            scalars = torch.empty(2, dtype=torch.float64, device=self.device)
+        ws, n = self.workspace(native.OP_GRADIENT_PROBED, probe)
+        native.tp_gradient_probed(self.grid, self.geom, probe.to_c(), _ptr(vel), _ptr(wavelet), _ptr(d_obs),
+                                  _ptr(grad), scalars.data_ptr(), scalars.data_ptr() + 8, ws, n, _stream())
+        return grad, scalars
+
+    def gradient_full(self, vel, wavelet, d_obs, grad=None, scalars=None):
+        vel, wavelet, d_obs = _f32(vel, self.device), _f32(wavelet, self.device), _f32(d_obs, self.device)
+        if grad is None:
+            grad = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        if scalars is None:
+            scalars = torch.empty(2, dtype=torch.float64, device=self.device)
+        ws, n = self.workspace(native.OP_GRADIENT_FULL)
+        native.tp_gradient_full(self.grid, self.geom, _ptr(vel), _ptr(wavelet), _ptr(d_obs), _ptr(grad),
+                                scalars.data_ptr(), scalars.data_ptr() + 8, ws, n, _stream())
+        return grad, scalars
+
+    def probes(self, probe: ProbeSpec, shot: int = 0, nt: Optional[int] = None):
+        nt = self.nt if nt is None else nt
+        Z = torch.empty((nt, probe.r), dtype=torch.float32, device=self.device)
+        native.tp_probes(probe.to_c(), nt, shot, _ptr(Z), _stream())
+        return Z
+
+    def status(self, op: int):
+        """Raises if a bounded device-side wait of the last `op` call timed out."""
+        buf = self._ws.get(op)
+        if buf is None:
+            return
+        p = buf.data_ptr()
+        p += (-p) % 256
+        native.tp_workspace_status(p, buf.numel() - 256, _stream())
+
+
+def memory_model(problem: Problem, probe: ProbeSpec) -> dict:
+    """Gradient memory: the paper's counts (N nt values for the history,
+    2 N r for the probed accumulators) and this library's workspace bytes."""
+    N, nt, r, S = problem.N, problem.nt, probe.r, problem.nshots
+    return {
+        "full_history_values": N * nt * S,
+        "probed_accumulator_values": 2 * N * r * S,
+        "paper_reduction_factor": nt / (2.0 * r),
+        "workspace_full_bytes": problem.workspace_bytes(native.OP_GRADIENT_FULL),
+        "workspace_probed_bytes": problem.workspace_bytes(native.OP_GRADIENT_PROBED, probe),
+    }

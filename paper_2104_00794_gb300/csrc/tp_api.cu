@@ -1,0 +1,593 @@
+// C ABI of libtprobe (include/tprobe.h): argument checks, workspace layout
+// and the host-side time loops that enqueue the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tp_internal.h"
+#include "tprobe.h"
+
+namespace tp {
+
+namespace {
+
+thread_local std::string g_err;
+
+tp_status fail(tp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define TRY(expr)                                                                           \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) return fail(TP_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+constexpr int NBLK = 1024;       // partial sums of the fp64 reductions
+constexpr size_t SCAL_BYTES = 256;  // err flag, vmax bits, fallback scalars
+
+struct Scal {
+  int err;
+  unsigned int vmax_bits;
+  int pad[2];
+  double misfit, gnorm;
+};
+
+// ------------------------------------------------------------------ profiling
+struct Prof {
+  std::mutex m;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  size_t used = 0;
+  bool open = false;
+};
+Prof g_prof;
+
+}  // namespace
+
+void prof_before(int kind, cudaStream_t s) {
+  if (!g_prof.on) return;
+  std::lock_guard<std::mutex> lk(g_prof.m);
+  if (!g_prof.on || g_prof.used + 2 > g_prof.ev.size()) return;
+  cudaEventRecord(g_prof.ev[g_prof.used], s);
+  g_prof.kind[g_prof.used / 2] = kind;
+  g_prof.open = true;
+}
+
+void prof_after(int, cudaStream_t s) {
+  if (!g_prof.on) return;
+  std::lock_guard<std::mutex> lk(g_prof.m);
+  if (!g_prof.on || !g_prof.open) return;
+  cudaEventRecord(g_prof.ev[g_prof.used + 1], s);
+  g_prof.used += 2;
+  g_prof.open = false;
+}
+
+Layout make_layout(int ndim, int nx, int ny, int nz) {
+  Layout L;
+  L.ndim = ndim;
+  L.nx = nx;
+  L.ny = ny;
+  L.nz = nz;
+  L.px = (int)round_up(nx, XALIGN) + 2 * H;
+  L.py = ndim == 3 ? (int)round_up(ny, YALIGN) + 2 * H : 1;
+  L.pz = nz + 2 * H;
+  L.plane = (long long)L.py * L.px;
+  L.field = round_up((long long)L.pz * L.plane, 64);
+  return L;
+}
+
+// Centred second-derivative weights (Fornberg 1988, Table 1).
+Weights stencil_weights(int order) {
+  Weights W{};
+  if (order == 4) {
+    W.R = 2;
+    W.w[0] = -5.0f / 2.0f;
+    W.w[1] = 4.0f / 3.0f;
+    W.w[2] = -1.0f / 12.0f;
+  } else {
+    W.R = 4;
+    W.w[0] = (float)(-205.0 / 72.0);
+    W.w[1] = (float)(8.0 / 5.0);
+    W.w[2] = (float)(-1.0 / 5.0);
+    W.w[3] = (float)(8.0 / 315.0);
+    W.w[4] = (float)(-1.0 / 560.0);
+  }
+  return W;
+}
+
+namespace {
+
+struct Plan {
+  int op = 0;
+  Layout L{};
+  Weights W{};
+  int nshots = 0, nsrc = 0, nrec = 0, nt = 0, r = 0, T = 0, S = 0, kind = 0;
+  float scale = 1.f;
+  size_t bytes = 0;
+  size_t o_scal = 0, o_part = 0, o_c2 = 0, o_f = 0, o_P = 0, o_V = 0, o_Q = 0, o_d = 0, o_soff = 0, o_roff = 0,
+         o_cs = 0, o_cr = 0, o_qbar = 0, o_gacc = 0, o_sacc = 0;
+  long long nf = 0;  // fields in the wavefield block
+};
+
+size_t take(size_t& cur, size_t bytes) {
+  const size_t o = cur;
+  cur += (size_t)round_up((long long)bytes, 256);
+  return o;
+}
+
+tp_status check_grid(const tp_grid* g) {
+  if (!g) return fail(TP_ERR_ARG, "grid is NULL");
+  if (g->ndim != 2 && g->ndim != 3) return fail(TP_ERR_ARG, "ndim must be 2 or 3 (got %d)", g->ndim);
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(TP_ERR_ARG, "grid extents must be >= 1");
+  if (g->ndim == 2 && g->ny != 1) return fail(TP_ERR_ARG, "2-D grids need ny == 1 (got %d)", g->ny);
+  if (g->order != 4 && g->order != 8) return fail(TP_ERR_ARG, "order must be 4 or 8 (got %d)", g->order);
+  if (!(g->h > 0.f) || !(g->dt > 0.f)) return fail(TP_ERR_ARG, "h and dt must be positive");
+  if (g->nt < 3) return fail(TP_ERR_ARG, "nt must be >= 3 (got %d)", g->nt);
+  if ((long long)g->nx * g->ny * g->nz > (1LL << 40)) return fail(TP_ERR_ARG, "grid too large");
+  if (g->nx > (1 << 24) || g->nz > (1 << 24) || g->ny > (1 << 24)) return fail(TP_ERR_ARG, "grid extent too large");
+  if (!(g->vmax >= 0.f)) return fail(TP_ERR_ARG, "vmax must be >= 0");
+  return TP_OK;
+}
+
+tp_status check_geom(const tp_geom* g) {
+  if (!g) return fail(TP_ERR_ARG, "geom is NULL");
+  if (g->nshots < 1 || g->nsrc < 1 || g->nrec < 1) return fail(TP_ERR_ARG, "nshots, nsrc, nrec must be >= 1");
+  if (!g->src || !g->rec) return fail(TP_ERR_ARG, "src/rec index arrays are NULL");
+  if ((long long)g->nshots * g->nrec > (1LL << 31) || (long long)g->nshots * g->nsrc > (1LL << 31))
+    return fail(TP_ERR_ARG, "too many sources or receivers");
+  return TP_OK;
+}
+
+tp_status check_probe(const tp_probe* p, int nt) {
+  if (!p) return fail(TP_ERR_ARG, "probe is NULL");
+  if (p->kind < 0 || p->kind > 3) return fail(TP_ERR_ARG, "unknown probe kind %d", p->kind);
+  if (p->r < 1 || p->r > 256) return fail(TP_ERR_ARG, "r must be in 1..256 (got %d)", p->r);
+  if (p->kind == TP_PROBE_IDENTITY && p->r != nt) return fail(TP_ERR_ARG, "identity probes need r == nt");
+  if (p->kind == TP_PROBE_USER && !p->Z_user) return fail(TP_ERR_ARG, "user probes need Z_user");
+  if (p->T != 32 && p->T != 64) return fail(TP_ERR_ARG, "window T must be 32 or 64 (got %d)", p->T);
+  if (!(p->scale >= 0.f)) return fail(TP_ERR_ARG, "scale must be >= 0");
+  return TP_OK;
+}
+
+tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe* pr, Plan* P) {
+  tp_status st = check_grid(g);
+  if (st != TP_OK) return st;
+  if ((st = check_geom(geo)) != TP_OK) return st;
+  if (op < TP_OP_FORWARD || op > TP_OP_GRADIENT_FULL) return fail(TP_ERR_ARG, "unknown op %d", op);
+  if (op == TP_OP_GRADIENT_PROBED && (st = check_probe(pr, g->nt)) != TP_OK) return st;
+  P->op = op;
+  P->L = make_layout(g->ndim, g->nx, g->ny, g->nz);
+  P->W = stencil_weights(g->order);
+  P->nshots = geo->nshots;
+  P->nsrc = geo->nsrc;
+  P->nrec = geo->nrec;
+  P->nt = g->nt;
+  const size_t fb = (size_t)P->L.field * sizeof(float);
+  const long long ns = P->nshots;
+  size_t cur = 0;
+  P->o_scal = take(cur, SCAL_BYTES);
+  P->o_part = take(cur, NBLK * sizeof(double));
+  P->o_soff = take(cur, (size_t)ns * P->nsrc * sizeof(long long));
+  P->o_roff = take(cur, (size_t)ns * P->nrec * sizeof(long long));
+  P->o_cs = take(cur, (size_t)ns * P->nsrc * sizeof(float));
+  P->o_cr = take(cur, (size_t)ns * P->nrec * sizeof(float));
+  P->o_c2 = take(cur, fb);
+  switch (op) {
+    case TP_OP_FORWARD:
+    case TP_OP_ADJOINT:
+      P->nf = 3 * ns;
+      P->o_f = take(cur, (size_t)P->nf * fb);
+      break;
+    case TP_OP_GRADIENT_PROBED: {
+      P->kind = pr->kind;
+      P->r = pr->r;
+      P->T = pr->T;
+      P->S = P->T + 2;
+      P->scale = pr->scale > 0.f ? pr->scale
+                                 : ((pr->kind == TP_PROBE_RADEMACHER || pr->kind == TP_PROBE_GAUSSIAN) ? 1.0f / pr->r : 1.0f);
+      P->nf = (long long)P->S * ns;
+      P->o_f = take(cur, (size_t)P->nf * fb);
+      P->o_P = take(cur, (size_t)ns * P->r * fb);
+      P->o_V = take(cur, (size_t)ns * P->r * fb);
+      P->o_Q = take(cur, (size_t)ns * P->nt * P->r * sizeof(float));
+      P->o_d = take(cur, (size_t)ns * P->nt * P->nrec * sizeof(float));
+      P->o_qbar = take(cur, (size_t)ns * P->nsrc * P->r * sizeof(float));
+      P->o_gacc = take(cur, (size_t)ns * fb);
+      break;
+    }
+    case TP_OP_GRADIENT_FULL:
+      P->nf = (long long)P->nt * ns;
+      P->o_f = take(cur, (size_t)P->nf * fb);   // forward history, levels 0..nt-1
+      P->o_P = take(cur, (size_t)3 * ns * fb);  // adjoint levels
+      P->o_d = take(cur, (size_t)ns * P->nt * P->nrec * sizeof(float));
+      P->o_gacc = take(cur, (size_t)ns * fb);
+      P->o_sacc = take(cur, (size_t)ns * P->nsrc * sizeof(double));
+      break;
+  }
+  P->bytes = cur;
+  return TP_OK;
+}
+
+// Courant number above which the leapfrog scheme with this Laplacian grows:
+// (v dt / h)^2 * ndim * |S(pi)| <= 4, S(pi) the 1-D stencil symbol at Nyquist.
+double cfl_limit(const Plan& P) {
+  double sym = P.W.w[0];
+  for (int k = 1; k <= P.W.R; ++k) sym += 2.0 * P.W.w[k] * ((k & 1) ? -1.0 : 1.0);
+  return 2.0 / std::sqrt(P.L.ndim * std::fabs(sym));
+}
+
+struct Ctx {
+  const Plan& P;
+  char* ws;
+  cudaStream_t st;
+  template <class T> T* at(size_t o) const { return reinterpret_cast<T*>(ws + o); }
+  Scal* scal() const { return at<Scal>(P.o_scal); }
+  int* err() const { return &scal()->err; }
+  float* field(size_t base, long long i) const { return at<float>(base) + i * P.L.field; }
+};
+
+tp_status check_ws(const Plan& P, void* ws, size_t ws_bytes) {
+  if (!ws) return fail(TP_ERR_ARG, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(TP_ERR_ARG, "workspace must be 256-byte aligned");
+  if (ws_bytes < P.bytes) return fail(TP_ERR_NOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, P.bytes);
+  return TP_OK;
+}
+
+// Common set-up: coefficient field, point offsets, CFL check.
+tp_status setup(const Ctx& c, const tp_grid* g, const tp_geom* geo, const float* vel) {
+  const Plan& P = c.P;
+  if (!vel) return fail(TP_ERR_ARG, "vel is NULL");
+  TRY(cudaMemsetAsync(c.scal(), 0, SCAL_BYTES, c.st));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_c2), 0, (size_t)P.L.field * sizeof(float), c.st));
+  const float dt2 = g->dt * g->dt;
+  TRY(launch_prep_c2(P.L, vel, dt2 / (g->h * g->h), c.at<float>(P.o_c2), c.st));
+  TRY(launch_prep_points(P.L, geo->src, (long long)P.nshots * P.nsrc, vel, dt2, c.at<long long>(P.o_soff),
+                         c.at<float>(P.o_cs), c.err(), c.st));
+  TRY(launch_prep_points(P.L, geo->rec, (long long)P.nshots * P.nrec, vel, dt2, c.at<long long>(P.o_roff),
+                         c.at<float>(P.o_cr), c.err(), c.st));
+  float vmax = g->vmax;
+  if (!(vmax > 0.f)) {
+    TRY(launch_vmax(vel, (long long)g->nx * g->ny * g->nz, &c.scal()->vmax_bits, c.st));
+    Scal host{};
+    TRY(cudaMemcpyAsync(&host, c.scal(), sizeof(Scal), cudaMemcpyDeviceToHost, c.st));
+    TRY(cudaStreamSynchronize(c.st));
+    if (host.err & 2) return fail(TP_ERR_ARG, "a source or receiver index lies outside the grid");
+    uint32_t bits = host.vmax_bits;
+    memcpy(&vmax, &bits, sizeof(vmax));
+  }
+  const double courant = (double)vmax * g->dt / g->h;
+  if (!(courant <= cfl_limit(P)))
+    return fail(TP_ERR_UNSTABLE, "CFL: vmax*dt/h = %.4f exceeds the stability limit %.4f", courant, cfl_limit(P));
+  return TP_OK;
+}
+
+tp_status step(const Ctx& c, const float* cur, const float* old, float* out, long long ss) {
+  StencilArgs a{cur, ss, old, ss, c.at<float>(c.P.o_c2), 0, out, ss, c.P.nshots};
+  TRY(launch_stencil(MODE_STEP, c.P.L, c.P.W, a, c.st));
+  return TP_OK;
+}
+
+// sampling of `samp` at offsets soff into out (may be null), injection into `inj`
+tp_status point(const Ctx& c, const float* samp, long long samp_ss, const long long* soff, int nsamp, float* out,
+                long long out_ss, float* inj, long long inj_ss, const long long* ioff, const float* icoef, int ninj,
+                const float* ival, long long ival_ss, double* acc = nullptr, const float* aval = nullptr,
+                long long aval_ss = 0) {
+  PointArgs a{};
+  a.nshots = c.P.nshots;
+  a.field_samp = samp; a.samp_ss = samp_ss; a.samp_off = soff; a.nsamp = samp ? nsamp : 0;
+  a.samp_out = out; a.samp_out_ss = out_ss;
+  a.field_inj = inj; a.inj_ss = inj_ss; a.inj_off = ioff; a.inj_coef = icoef; a.ninj = inj ? ninj : 0;
+  a.inj_val = ival; a.inj_val_ss = ival_ss;
+  a.acc = acc; a.acc_val = aval; a.acc_val_ss = aval_ss;
+  TRY(launch_point(a, c.st));
+  return TP_OK;
+}
+
+#define TRYS(expr)                    \
+  do {                                \
+    tp_status s_ = (expr);            \
+    if (s_ != TP_OK) return s_;       \
+  } while (0)
+
+// Forward loop (Algorithm 1 lines 0-3).  level(t) gives the shot-0 field of
+// level t; `ss` is the shot stride.  d (may be null) receives R u[t];
+// after_level(t) runs once level t is complete (sources injected).
+template <class LevelFn, class AfterFn>
+tp_status forward_loop(const Ctx& c, LevelFn level, long long ss, const float* wav, float* d, AfterFn after_level) {
+  const Plan& P = c.P;
+  const long long dss = (long long)P.nt * P.nrec, wss = (long long)P.nt * P.nsrc;
+  for (int t = 1; t <= P.nt - 2; ++t) {
+    TRYS(step(c, level(t), level(t - 1), level(t + 1), ss));
+    TRYS(point(c, d ? level(t) : nullptr, ss, c.at<long long>(P.o_roff), P.nrec, d ? d + (long long)t * P.nrec : nullptr,
+               dss, level(t + 1), ss, c.at<long long>(P.o_soff), c.at<float>(P.o_cs), P.nsrc,
+               wav + (long long)t * P.nsrc, wss));
+    TRYS(after_level(t + 1));
+  }
+  if (d)
+    TRYS(point(c, level(P.nt - 1), ss, c.at<long long>(P.o_roff), P.nrec, d + (long long)(P.nt - 1) * P.nrec, dss,
+               nullptr, 0, nullptr, nullptr, 0, nullptr, 0));
+  return TP_OK;
+}
+
+// Adjoint loop (Algorithm 1 lines 4-7) driven by s[nshots][nt][nrec].
+// q_out (may be null) receives S lambda[t+1] at row t; acc/aval accumulate
+// sum_k lambda[k][src] q[k-1] for the full gradient's source term.
+template <class LevelFn, class AfterFn>
+tp_status adjoint_loop(const Ctx& c, LevelFn level, long long ss, const float* s, float* q_out, double* acc,
+                       const float* aval, AfterFn after_level) {
+  const Plan& P = c.P;
+  const long long sss = (long long)P.nt * P.nrec, qss = (long long)P.nt * P.nsrc;
+  const bool samp = q_out || acc;
+  for (int j = P.nt - 1; j >= 2; --j) {
+    TRYS(step(c, level(j + 1), level(j + 2), level(j), ss));
+    TRYS(point(c, samp ? level(j + 1) : nullptr, ss, c.at<long long>(P.o_soff), P.nsrc,
+               q_out ? q_out + (long long)j * P.nsrc : nullptr, qss, level(j), ss, c.at<long long>(P.o_roff),
+               c.at<float>(P.o_cr), P.nrec, s + (long long)j * P.nrec, sss, acc,
+               aval ? aval + (long long)j * P.nsrc : nullptr, qss));
+    TRYS(after_level(j));
+  }
+  if (samp)
+    TRYS(point(c, level(2), ss, c.at<long long>(P.o_soff), P.nsrc, q_out ? q_out + P.nsrc : nullptr, qss, nullptr, 0,
+               nullptr, nullptr, 0, nullptr, 0, acc, aval ? aval + P.nsrc : nullptr, qss));
+  return TP_OK;
+}
+
+tp_status misfit_and_residual(const Ctx& c, float* d, const float* dobs, double* misfit) {
+  const Plan& P = c.P;
+  if (!dobs) return fail(TP_ERR_ARG, "d_obs is NULL");
+  double* part = c.at<double>(P.o_part);
+  TRY(launch_residual(d, dobs, (long long)P.nshots * P.nt * P.nrec, part, NBLK, c.st));
+  TRY(launch_finalize_sum(part, NBLK, 0.5, misfit ? misfit : &c.scal()->misfit, 0, c.err(), c.st));
+  return TP_OK;
+}
+
+tp_status grad_norm(const Ctx& c, const float* grad, double* gnorm) {
+  const Plan& P = c.P;
+  double* part = c.at<double>(P.o_part);
+  TRY(launch_sumsq(grad, (long long)P.L.nx * P.L.ny * P.L.nz, part, NBLK, c.st));
+  TRY(launch_finalize_sum(part, NBLK, 1.0, gnorm ? gnorm : &c.scal()->gnorm, 1, c.err(), c.st));
+  return TP_OK;
+}
+
+}  // namespace
+}  // namespace tp
+
+using namespace tp;
+
+extern "C" {
+
+size_t tp_workspace_bytes(int op, const tp_grid* grid, const tp_geom* geom, const tp_probe* probe) {
+  Plan P;
+  if (make_plan(op, grid, geom, probe, &P) != TP_OK) return 0;
+  return P.bytes;
+}
+
+tp_status tp_forward(const tp_grid* grid, const tp_geom* geom, const float* vel, const float* wavelet, float* d_out,
+                     void* ws, size_t ws_bytes, void* stream) {
+  Plan P;
+  TRYS(make_plan(TP_OP_FORWARD, grid, geom, nullptr, &P));
+  TRYS(check_ws(P, ws, ws_bytes));
+  if (!wavelet || !d_out) return fail(TP_ERR_ARG, "wavelet/d_out is NULL");
+  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
+  TRYS(setup(c, grid, geom, vel));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * P.L.field * sizeof(float), c.st));
+  TRY(cudaMemsetAsync(d_out, 0, (size_t)P.nshots * P.nt * P.nrec * sizeof(float), c.st));
+  const long long ss = 3 * P.L.field;
+  auto level = [&](int t) { return c.field(P.o_f, t % 3); };
+  TRYS(forward_loop(c, level, ss, wavelet, d_out, [](int) { return TP_OK; }));
+  return TP_OK;
+}
+
+tp_status tp_adjoint(const tp_grid* grid, const tp_geom* geom, const float* vel, const float* d_in, float* q_out,
+                     void* ws, size_t ws_bytes, void* stream) {
+  Plan P;
+  TRYS(make_plan(TP_OP_ADJOINT, grid, geom, nullptr, &P));
+  TRYS(check_ws(P, ws, ws_bytes));
+  if (!d_in || !q_out) return fail(TP_ERR_ARG, "d_in/q_out is NULL");
+  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
+  TRYS(setup(c, grid, geom, vel));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * P.L.field * sizeof(float), c.st));
+  TRY(cudaMemsetAsync(q_out, 0, (size_t)P.nshots * P.nt * P.nsrc * sizeof(float), c.st));
+  const long long ss = 3 * P.L.field;
+  auto level = [&](int t) { return c.field(P.o_f, t % 3); };
+  TRYS(adjoint_loop(c, level, ss, d_in, q_out, nullptr, nullptr, [](int) { return TP_OK; }));
+  return TP_OK;
+}
+
+tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe, const float* vel,
+                             const float* wavelet, const float* d_obs, float* grad, double* misfit, double* gnorm,
+                             void* ws, size_t ws_bytes, void* stream) {
+  Plan P;
+  TRYS(make_plan(TP_OP_GRADIENT_PROBED, grid, geom, probe, &P));
+  TRYS(check_ws(P, ws, ws_bytes));
+  if (!wavelet || !d_obs || !grad) return fail(TP_ERR_ARG, "wavelet/d_obs/grad is NULL");
+  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
+  TRYS(setup(c, grid, geom, vel));
+  const size_t fb = (size_t)P.L.field * sizeof(float);
+  const int nt = P.nt, T = P.T, S = P.S, r = P.r;
+  const long long ring_ss = (long long)S * P.L.field;
+  TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_P), 0, (size_t)P.nshots * r * fb, c.st));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_V), 0, (size_t)P.nshots * r * fb, c.st));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_gacc), 0, (size_t)P.nshots * fb, c.st));
+  float* d = c.at<float>(P.o_d);
+  TRY(cudaMemsetAsync(d, 0, (size_t)P.nshots * nt * P.nrec * sizeof(float), c.st));
+  float* Q = c.at<float>(P.o_Q);
+  TRY(launch_probes(P.kind, nt, r, probe->seed, 0, P.nshots, probe->Z_user, Q, c.st));
+  auto level = [&](int t) { return c.field(P.o_f, t % S); };
+
+  GemmArgs g{};
+  g.ring = c.at<float>(P.o_f); g.slot_stride = P.L.field; g.ring_ss = ring_ss; g.nslots = S;
+  g.Q = Q; g.nt = nt; g.r = r; g.q_ss = (long long)nt * r;
+  g.M = P.L.field; g.nshots = P.nshots; g.qlo = 2; g.qhi = nt - 1;
+  g.q_has_lo = (P.kind == TP_PROBE_GAUSSIAN || P.kind == TP_PROBE_USER) ? 1 : 0;
+  g.err = c.err();
+
+  // forward: P_s[:, i] = sum_{j=2}^{nt-2} Q_s[j+1, i] u_s[j]  (windows of T levels)
+  g.P = c.at<float>(P.o_P); g.p_ss = (long long)r * P.L.field; g.qshift = 1;
+  const int jlast = nt - 2;
+  auto fwd_after = [&](int lev) -> tp_status {
+    if (lev < 2 || lev > jlast) return TP_OK;
+    const int w0 = 2 + ((lev - 2) / T) * T;
+    if (lev == std::min(w0 + T - 1, jlast)) {
+      g.level0 = w0;
+      g.nlev = lev - w0 + 1;
+      TRY(launch_probe_gemm(g, c.st));
+    }
+    return TP_OK;
+  };
+  TRYS(forward_loop(c, level, ring_ss, wavelet, d, fwd_after));
+  TRYS(misfit_and_residual(c, d, d_obs, misfit));
+
+  // adjoint: V_s[:, i] = sum_{k=2}^{nt-1} Q_s[k, i] lambda_s[k]  (windows from the top)
+  for (int k = nt; k <= nt + 1; ++k)
+    for (int s = 0; s < P.nshots; ++s)
+      TRY(cudaMemsetAsync(level(k) + s * ring_ss, 0, fb, c.st));
+  g.P = c.at<float>(P.o_V); g.qshift = 0;
+  auto adj_after = [&](int lev) -> tp_status {
+    const int top = nt - 1 - ((nt - 1 - lev) / T) * T;
+    const int bottom = std::max(2, top - T + 1);
+    if (lev == bottom) {
+      g.level0 = bottom;
+      g.nlev = top - bottom + 1;
+      TRY(launch_probe_gemm(g, c.st));
+    }
+    return TP_OK;
+  };
+  TRYS(adjoint_loop(c, level, ring_ss, d, nullptr, nullptr, nullptr, adj_after));
+
+  // combine (Algorithm 1 line 8): ubar = v^2 (L P + S^T qbar), grad = -scale sum_i ubar vbar
+  const long long pss = (long long)r * P.L.field;
+  for (int i = 0; i < r; ++i) {
+    StencilArgs a{c.field(P.o_P, i), pss, c.field(P.o_V, i), pss, c.at<float>(P.o_gacc), P.L.field,
+                  c.at<float>(P.o_gacc), P.L.field, P.nshots};
+    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st));
+  }
+  TRY(launch_finish_grad(P.L, vel, c.at<float>(P.o_gacc), P.nshots, P.L.field, P.scale / (grid->h * grid->h), grad,
+                         c.st));
+  TRY(launch_qbar(Q, nt, r, wavelet, P.nsrc, P.nshots, 1, nt - 2, 1, c.at<float>(P.o_qbar), c.st));
+  TRY(launch_source_term(P.L, vel, geom->src, c.at<long long>(P.o_soff), P.nsrc, P.nshots, P.scale,
+                         c.at<float>(P.o_qbar), c.at<float>(P.o_V), r, pss, nullptr, grad, c.st));
+  TRYS(grad_norm(c, grad, gnorm));
+  return TP_OK;
+}
+
+tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float* vel, const float* wavelet,
+                           const float* d_obs, float* grad, double* misfit, double* gnorm, void* ws, size_t ws_bytes,
+                           void* stream) {
+  Plan P;
+  TRYS(make_plan(TP_OP_GRADIENT_FULL, grid, geom, nullptr, &P));
+  TRYS(check_ws(P, ws, ws_bytes));
+  if (!wavelet || !d_obs || !grad) return fail(TP_ERR_ARG, "wavelet/d_obs/grad is NULL");
+  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
+  TRYS(setup(c, grid, geom, vel));
+  const size_t fb = (size_t)P.L.field * sizeof(float);
+  const int nt = P.nt;
+  const long long hist_ss = (long long)nt * P.L.field, lam_ss = 3 * P.L.field;
+  TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_P), 0, (size_t)3 * P.nshots * fb, c.st));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_gacc), 0, (size_t)P.nshots * fb, c.st));
+  TRY(cudaMemsetAsync(c.at<double>(P.o_sacc), 0, (size_t)P.nshots * P.nsrc * sizeof(double), c.st));
+  float* d = c.at<float>(P.o_d);
+  TRY(cudaMemsetAsync(d, 0, (size_t)P.nshots * nt * P.nrec * sizeof(float), c.st));
+  auto hist = [&](int t) { return c.field(P.o_f, t); };
+  TRYS(forward_loop(c, hist, hist_ss, wavelet, d, [](int) { return TP_OK; }));
+  TRYS(misfit_and_residual(c, d, d_obs, misfit));
+  // adjoint with the imaging condition of Eq. 3 in its stencil form:
+  // gacc_s += lambda_s[j] * S(u_s[j-1])   (udd[j] = v^2 (L u[j-1] + S^T q[j-1]))
+  auto lam = [&](int k) { return c.field(P.o_P, k % 3); };
+  auto imaging = [&](int j) -> tp_status {
+    StencilArgs a{hist(j - 1), hist_ss, lam(j), lam_ss, c.at<float>(P.o_gacc), P.L.field, c.at<float>(P.o_gacc),
+                  P.L.field, P.nshots};
+    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st));
+    return TP_OK;
+  };
+  TRYS(adjoint_loop(c, lam, lam_ss, d, nullptr, c.at<double>(P.o_sacc), wavelet, imaging));
+  TRY(launch_finish_grad(P.L, vel, c.at<float>(P.o_gacc), P.nshots, P.L.field, 1.0f / (grid->h * grid->h), grad,
+                         c.st));
+  TRY(launch_source_term(P.L, vel, geom->src, c.at<long long>(P.o_soff), P.nsrc, P.nshots, 1.0f, nullptr, nullptr, 0,
+                         0, c.at<double>(P.o_sacc), grad, c.st));
+  TRYS(grad_norm(c, grad, gnorm));
+  return TP_OK;
+}
+
+tp_status tp_probes(const tp_probe* probe, int nt, int shot, float* Z, void* stream) {
+  if (nt < 1) return fail(TP_ERR_ARG, "nt must be >= 1");
+  TRYS(check_probe(probe, nt));
+  if (!Z || shot < 0) return fail(TP_ERR_ARG, "Z is NULL or shot < 0");
+  const float* zu = probe->Z_user ? probe->Z_user + (long long)shot * nt * probe->r : nullptr;
+  TRY(launch_probes(probe->kind, nt, probe->r, probe->seed, shot, 1, zu, Z, static_cast<cudaStream_t>(stream)));
+  return TP_OK;
+}
+
+tp_status tp_workspace_status(void* ws, size_t ws_bytes, void* stream) {
+  if (!ws || ws_bytes < SCAL_BYTES) return fail(TP_ERR_ARG, "workspace is NULL or too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int flag = 0;
+  TRY(cudaMemcpyAsync(&flag, ws, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TRY(cudaStreamSynchronize(st));
+  TRY(cudaMemsetAsync(ws, 0, sizeof(int), st));
+  if (flag & 1) return fail(TP_ERR_TIMEOUT, "a bounded device-side wait timed out");
+  if (flag & 2) return fail(TP_ERR_ARG, "a source or receiver index lies outside the grid");
+  return TP_OK;
+}
+
+const char* tp_last_error(void) { return g_err.c_str(); }
+
+tp_status tp_profile_begin(int max_launches) {
+  std::lock_guard<std::mutex> lk(g_prof.m);
+  if (g_prof.on) return fail(TP_ERR_ARG, "profiling already active");
+  const size_t n = (size_t)(max_launches > 0 ? max_launches : 65536);
+  if (g_prof.ev.size() < 2 * n) {
+    size_t have = g_prof.ev.size();
+    g_prof.ev.resize(2 * n);
+    for (size_t i = have; i < 2 * n; ++i) TRY(cudaEventCreate(&g_prof.ev[i]));
+  }
+  g_prof.kind.assign(n, 0);
+  g_prof.used = 0;
+  g_prof.open = false;
+  g_prof.on = true;
+  return TP_OK;
+}
+
+tp_status tp_profile_end(double* ms, int64_t* launches) {
+  std::lock_guard<std::mutex> lk(g_prof.m);
+  if (!g_prof.on) return fail(TP_ERR_ARG, "profiling not active");
+  g_prof.on = false;
+  for (int k = 0; k < TP_KERNEL_KINDS; ++k) {
+    if (ms) ms[k] = 0.0;
+    if (launches) launches[k] = 0;
+  }
+  for (size_t i = 0; i < g_prof.used; i += 2) {
+    TRY(cudaEventSynchronize(g_prof.ev[i + 1]));
+    float t = 0.f;
+    TRY(cudaEventElapsedTime(&t, g_prof.ev[i], g_prof.ev[i + 1]));
+    const int k = g_prof.kind[i / 2];
+    if (ms) ms[k] += t;
+    if (launches) launches[k] += 1;
+  }
+  return TP_OK;
+}
+
+const char* tp_kernel_name(int kind) {
+  static const char* names[TP_KERNEL_KINDS] = {"stencil_step", "imaging_sweep", "probe_gemm_tcgen05",
+                                               "point_inject_sample", "reduce_fp64", "setup_other"};
+  return (kind >= 0 && kind < TP_KERNEL_KINDS) ? names[kind] : "unknown";
+}
+
+}  // extern "C"

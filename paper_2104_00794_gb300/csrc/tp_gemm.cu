@@ -1,0 +1,268 @@
+// Windowed probe GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Algorithm 1 accumulates, at every time level k, ubar[x,:] += Q[k,:] * w_k[x]
+// (lines 2 and 6).  Over a window of T levels this is the dense contraction
+//     P[x, i] += sum_{k in window} W[x, k] * Q[k, i],
+// M = grid points (10^4 .. 2*10^7), K = T (32/64), N = r (4..256), with W the
+// T ring snapshots that the stencil sweeps already wrote.  Per CTA tile of 128
+// points:
+//   1. 128 threads load the tile's T snapshot values (coalesced rows of 128
+//      points per level), split each fp32 value into tf32 hi + lo parts and
+//      store both into shared memory in the K-major, no-swizzle core-matrix
+//      layout (8 rows x 16 B core matrices);
+//   2. one thread issues tcgen05.mma kind::tf32 (M=128, N=round16(r), K=8 per
+//      instruction): hi*Qhi + lo*Qhi (+ hi*Qlo for probes that are not exact
+//      in tf32), accumulating in TMEM;
+//   3. tcgen05.commit arrives on an mbarrier; all warps wait (bounded), read
+//      their 32 TMEM lanes with tcgen05.ld and add the tile into P in HBM.
+// The hi/lo split keeps ~22 significant bits of the snapshots, so the product
+// is accurate to a few 1e-7 relative; Rademacher / identity probes are exact
+// in tf32 and skip the third MMA.
+#include <algorithm>
+
+#include "tp_internal.h"
+
+namespace tp {
+
+namespace {
+
+constexpr int TILE_M = 128;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded spin
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-dimension
+// byte offset (between K-adjacent core matrices), stride-dimension byte offset
+// (between M/N-adjacent 8-row groups), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle operand with KP
+// columns: core matrix (row/8, k/4) at ((row/8)*(KP/4) + k/4)*128, row%8 at
+// 16 B steps, k%4 at 4 B steps.  => LBO = 128 B, SBO = KP*32 B.
+__device__ __forceinline__ uint32_t kmaj_off(int row, int k, int KP) {
+  return (uint32_t)((((row >> 3) * (KP >> 2) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+}
+
+template <int KP>
+__global__ void __launch_bounds__(TILE_M, 1)
+probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  // layout: A_hi | A_lo | B_hi | B_lo | mbarrier | tmem slot
+  const uint32_t a_bytes = TILE_M * KP * 4, b_bytes = (uint32_t)NP * KP * 4;
+  unsigned char* A_hi = smem;
+  unsigned char* A_lo = smem + a_bytes;
+  unsigned char* B_hi = smem + 2 * a_bytes;
+  unsigned char* B_lo = B_hi + b_bytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(B_lo + b_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int shot = blockIdx.y;
+  const float* ring = a.ring + shot * a.ring_ss;
+  const float* Q = a.Q + shot * a.q_ss;
+  float* P = a.P + shot * a.p_ss;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // B operand (probe block), once per CTA: B[n][k] = Q[level0 + k + qshift][n]
+  for (int e = tid; e < NP * KP; e += TILE_M) {
+    const int n = e / KP, k = e % KP;
+    const int row = a.level0 + k + a.qshift;
+    float v = 0.f;
+    if (n < a.r && k < a.nlev && row >= a.qlo && row <= a.qhi) v = Q[(long long)row * a.r + n];
+    const float hi = tf32_hi(v);
+    *reinterpret_cast<float*>(B_hi + kmaj_off(n, k, KP)) = hi;
+    *reinterpret_cast<float*>(B_lo + kmaj_off(n, k, KP)) = v - hi;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const uint32_t idesc = idesc_tf32(TILE_M, NP);
+  const uint32_t sbo = KP * 32, lbo = 128;
+  const uint32_t a_hi_u = smem_u32(A_hi), a_lo_u = smem_u32(A_lo);
+  const uint32_t b_hi_u = smem_u32(B_hi), b_lo_u = smem_u32(B_lo);
+  const uint32_t bar = smem_u32(mbar);
+  bool ok = true;
+  uint32_t phase = 0;
+
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long m0 = tile * TILE_M;
+    const long long pt = m0 + tid;
+    const bool in = pt < a.M;
+    // 1. stage A: row = this thread's point, K = the window's levels.  All
+    //    KP loads are issued before any is used (memory-level parallelism).
+    float v[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      v[k] = 0.f;
+      if (in && k < a.nlev) {
+        const int slot = (a.level0 + k) % a.nslots;
+        v[k] = __ldcs(ring + (long long)slot * a.slot_stride + pt);
+      }
+    }
+#pragma unroll
+    for (int k4 = 0; k4 < KP; k4 += 4) {
+      float4 hi, lo;
+      hi.x = tf32_hi(v[k4 + 0]); hi.y = tf32_hi(v[k4 + 1]); hi.z = tf32_hi(v[k4 + 2]); hi.w = tf32_hi(v[k4 + 3]);
+      lo.x = v[k4 + 0] - hi.x; lo.y = v[k4 + 1] - hi.y; lo.z = v[k4 + 2] - hi.z; lo.w = v[k4 + 3] - hi.w;
+      const uint32_t o = kmaj_off(tid, k4, KP);
+      *reinterpret_cast<float4*>(A_hi + o) = hi;
+      *reinterpret_cast<float4*>(A_lo + o) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // 2. one thread issues the MMAs
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < KP / 8; ++kk) {
+        const uint32_t ko = kk * 2 * 128;  // two 16-byte K chunks per MMA
+        const uint64_t ah = smem_desc(a_hi_u + ko, lbo, sbo), al = smem_desc(a_lo_u + ko, lbo, sbo);
+        const uint64_t bh = smem_desc(b_hi_u + ko, lbo, sbo), bl = smem_desc(b_lo_u + ko, lbo, sbo);
+        mma_tf32(tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
+        mma_tf32(tmem, al, bh, idesc, 1u);
+        if (a.q_has_lo) mma_tf32(tmem, ah, bl, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                   : "memory");
+    }
+    __syncwarp();
+    // 3. epilogue: TMEM lanes 32*warp.. -> P (coalesced per probe column)
+    const int all_done = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
+    if (!all_done) {
+      ok = false;
+      if (tid == 0) atomicExch(a.err, 1);
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const long long prow = m0 + warp * 32 + lane;
+      for (int c0 = 0; c0 < NP; c0 += 16) {
+        float acc[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+        if (prow < a.M) {
+          float old[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            old[j] = (c0 + j < a.r) ? P[(long long)(c0 + j) * a.M + prow] : 0.f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < a.r) P[(long long)(c0 + j) * a.M + prow] = old[j] + acc[j];
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  }
+}
+
+template <int KP>
+cudaError_t launch_kp(const GemmArgs& a, cudaStream_t s) {
+  const int NP = std::max(16, (a.r + 15) / 16 * 16);
+  int ncols = 32;
+  while (ncols < NP) ncols <<= 1;
+  const size_t smem = (size_t)2 * TILE_M * KP * 4 + (size_t)2 * NP * KP * 4 + 16;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(probe_gemm_tf32<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set = true;
+  }
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, probe_gemm_tf32<KP>, TILE_M, smem);
+  occ = std::max(1, std::min(occ, 512 / ncols));
+  const long long ntiles = (a.M + TILE_M - 1) / TILE_M;
+  const long long grid_x = std::min<long long>(ntiles, (long long)sms * occ);
+  dim3 grid((unsigned)grid_x, a.nshots);
+  probe_gemm_tf32<KP><<<grid, TILE_M, smem, s>>>(a, NP, ncols, ntiles);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int gemm_kpad(int T) { return T <= 32 ? 32 : 64; }
+
+cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
+  if (a.nlev <= 0) return cudaSuccess;
+  prof_before(2, s);  // TP_KERNEL_PROBE_GEMM
+  cudaError_t e = a.nlev <= 32 ? launch_kp<32>(a, s) : launch_kp<64>(a, s);
+  prof_after(2, s);
+  return e;
+}
+
+}  // namespace tp

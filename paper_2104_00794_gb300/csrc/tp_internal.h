@@ -1,0 +1,129 @@
+// Internal declarations shared by the translation units of libtprobe.
+// Not part of the public ABI (see include/tprobe.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tp {
+
+// Halo width of every padded field: zero layers around the grid that make
+// the Dirichlet boundary of the Laplacian free (covers radius R <= 4).
+constexpr int H = 4;
+// x extents are padded to a multiple of this (tile widths of the sweeps).
+constexpr int XALIGN = 128;
+// y extents (3-D) are padded to a multiple of this.
+constexpr int YALIGN = 16;
+
+// Geometry of a padded field.  Grid node (z, y, x) lives at
+//   (z + H) * plane + (y + yh) * px + (x + H),  yh = H in 3-D, 0 in 2-D.
+// Padding and halo cells are zero and never written by the kernels.
+struct Layout {
+  int ndim, nx, ny, nz;
+  int px, py, pz;       // padded extents (py = 1 in 2-D)
+  long long plane;      // py * px
+  long long field;      // pz * plane, rounded up to 64 floats (256 B)
+  __host__ __device__ long long off(long long z, long long y, long long x) const {
+    return (z + H) * plane + (y + (ndim == 3 ? H : 0)) * px + (x + H);
+  }
+  __host__ __device__ long long off_flat(long long idx) const {  // dense (z*ny+y)*nx+x
+    long long x = idx % nx, t = idx / nx;
+    long long y = t % ny, z = t / ny;
+    return off(z, y, x);
+  }
+};
+
+Layout make_layout(int ndim, int nx, int ny, int nz);
+
+// Centred second-derivative weights w[0..R] (Fornberg 1988) for order 2R.
+struct Weights {
+  float w[5];
+  int R;
+};
+Weights stencil_weights(int order);
+
+// ---------------------------------------------------------------- stencil
+enum StencilMode { MODE_STEP = 0, MODE_IMAGE = 1 };
+
+// MODE_STEP : out = 2 src - p1 + p2 * S(src)          (leapfrog, p1 = older level, p2 = c2)
+// MODE_IMAGE: out = p2 + p1 * S(src)  (out may alias p2: accumulate)
+// S(.) = sum of stencil weights (no 1/h^2).  Pointers are shot-0 bases;
+// *_ss are per-shot strides in floats (0 = shared by all shots).
+struct StencilArgs {
+  const float* src;  long long src_ss;
+  const float* p1;   long long p1_ss;
+  const float* p2;   long long p2_ss;
+  float* out;        long long out_ss;
+  int nshots;
+};
+cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& a,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------- probe GEMM
+// P[s][i][x] += sum_{k < nlev} ring[s][(level0 + k) mod nslots][x] * Q[s][level0 + k + qshift][i]
+// with Q rows outside [qlo, qhi] read as zero.  tcgen05 (kind::tf32) with a
+// hi/lo split of the snapshots (and of Q when q_has_lo).
+struct GemmArgs {
+  const float* ring; long long slot_stride; long long ring_ss; int nslots;
+  int level0, nlev, qshift, qlo, qhi;
+  const float* Q; int nt, r; long long q_ss;
+  float* P; long long M; long long p_ss;
+  int nshots;
+  int q_has_lo;
+  int* err;
+};
+cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s);
+int gemm_kpad(int T);
+
+// ---------------------------------------------------------------- misc kernels
+cudaError_t launch_prep_c2(const Layout& L, const float* vel, float coef, float* c2, cudaStream_t s);
+cudaError_t launch_vmax(const float* vel, long long n, unsigned int* out_bits, cudaStream_t s);
+// dense node indices -> padded offsets, and injection coefficient dt^2 v^2 at each point
+// (out-of-range indices get offset -1 and set bit 2 of *err)
+cudaError_t launch_prep_points(const Layout& L, const int64_t* idx, long long n, const float* vel,
+                               float dt2, long long* off, float* cinj, int* err, cudaStream_t s);
+
+// One thread per point of two independent sets, all shots:
+//   sample: samp_out[s][t_s][j] = field_samp[s][samp_off[s][j]]           (j < nsamp)
+//   inject: field_inj[s][inj_off[s][k]] += inj_coef[s][k] * inj_val[s][t_i][k]  (k < ninj)
+//   srcacc (optional): acc[s][j] += sampled value * acc_val[s][t_a][j]
+struct PointArgs {
+  int nshots;
+  const float* field_samp; long long samp_ss;
+  const long long* samp_off; int nsamp; float* samp_out; long long samp_out_ss;  // already offset to t
+  float* field_inj; long long inj_ss;
+  const long long* inj_off; const float* inj_coef; int ninj;
+  const float* inj_val; long long inj_val_ss;  // already offset to t
+  double* acc; const float* acc_val; long long acc_val_ss;  // may be null
+};
+cudaError_t launch_point(const PointArgs& a, cudaStream_t s);
+
+cudaError_t launch_probes(int kind, int nt, int r, uint64_t seed, int shot0, int nshots,
+                          const float* Z_user, float* Q, cudaStream_t s);
+
+// res = d - dobs (in place over d), partial sums of res^2 into part[nblk]
+cudaError_t launch_residual(float* d, const float* dobs, long long n, double* part, int nblk,
+                            cudaStream_t s);
+// part[block] = sum a^2 over a fixed grid-stride set
+cudaError_t launch_sumsq(const float* a, long long n, double* part, int nblk, cudaStream_t s);
+// out = scale * sum(part[0..nblk))  (fixed order; sqrt first if asked; NaN if *err & 1)
+cudaError_t launch_finalize_sum(const double* part, int nblk, double scale, double* out,
+                                int sqrt_result, const int* err, cudaStream_t s);
+// grad[x] = -scale_h2 * vel[x]^2 * sum_s gacc[s][off(x)]
+cudaError_t launch_finish_grad(const Layout& L, const float* vel, const float* gacc, int nshots,
+                               long long gacc_ss, float scale_h2, float* grad, cudaStream_t s);
+// qbar[s][k][i] = sum_{j=jlo}^{jhi} Q[s][j + qshift][i] * q[s][j][k]
+cudaError_t launch_qbar(const float* Q, int nt, int r, const float* wav, int nsrc, int nshots,
+                        int jlo, int jhi, int qshift, float* qbar, cudaStream_t s);
+// grad[src[s][k]] += -scale * vel^2 * (probed: sum_i qbar[s][k][i] vbar[s][i][off]; full: srcacc[s][k])
+// serial in a fixed order (deterministic when sources share a node)
+cudaError_t launch_source_term(const Layout& L, const float* vel, const int64_t* src_dense,
+                               const long long* src_off, int nsrc, int nshots, float scale,
+                               const float* qbar, const float* V, int r, long long v_ss,
+                               const double* srcacc, float* grad, cudaStream_t s);
+
+// ---------------------------------------------------------------- profiling
+void prof_before(int kind, cudaStream_t s);
+void prof_after(int kind, cudaStream_t s);
+
+}  // namespace tp

@@ -1,0 +1,279 @@
+// Leapfrog stencil sweeps (Algorithm 1 lines 1 and 5, operators f and f^T)
+// and the stencil-form imaging sweep, for 2-D and 3-D padded fields.
+//
+// Design (HBM-bound, ~16 B per grid point per step):
+//   * every CTA owns an x-y tile (3-D) or an x strip (2-D) and sweeps a chunk
+//     of z planes; each thread owns 4 consecutive x points (float4 access);
+//   * the z neighbours of the thread's points live in a register queue of
+//     2R+1 float4 values, the current plane (with its x/y halo) in shared
+//     memory, so each haloed value is read from L2/HBM about once per sweep;
+//   * all global loads of plane z+1 (queue head, halo, older level,
+//     coefficient) are issued before plane z is computed;
+//   * zero halo layers of the padded layout supply the Dirichlet boundary,
+//     so no load is predicated.
+#include <algorithm>
+
+#include "tp_internal.h"
+
+namespace tp {
+
+namespace {
+
+__device__ __forceinline__ float4 ld4(const float* base, long long idx) {
+  return __ldg(reinterpret_cast<const float4*>(base + idx));
+}
+
+template <int MODE>
+__device__ __forceinline__ float epilogue(float c, float s, float p1, float p2) {
+  if (MODE == MODE_STEP) return fmaf(p2, s, 2.0f * c - p1);
+  return fmaf(p1, s, p2);
+}
+
+__device__ __forceinline__ float comp(const float4& v, int p) {
+  return p == 0 ? v.x : (p == 1 ? v.y : (p == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ void store_masked(float* out, long long idx, float4 v, int x, int nx) {
+  if (x + 3 < nx) {
+    *reinterpret_cast<float4*>(out + idx) = v;
+  } else {
+    if (x + 0 < nx) out[idx + 0] = v.x;
+    if (x + 1 < nx) out[idx + 1] = v.y;
+    if (x + 2 < nx) out[idx + 2] = v.z;
+    if (x + 3 < nx) out[idx + 3] = v.w;
+  }
+}
+
+// ------------------------------------------------------------------ 3-D
+constexpr int T3X = 16;  // float4 columns per tile (64 points)
+constexpr int T3Y = 16;  // rows per tile
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(T3X * T3Y, 2)
+sweep3d(Layout L, Weights W, StencilArgs a, int bz, int nzc) {
+  __shared__ float4 sm[T3Y + 2 * R][T3X + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int shot = blockIdx.z / nzc, zc = blockIdx.z % nzc;
+  const int x0 = blockIdx.x * (4 * T3X), y0 = blockIdx.y * T3Y;
+  const int x = x0 + 4 * tx, y = y0 + ty;
+  const int zb = zc * bz, ze = min(L.nz, zb + bz);
+  if (zb >= ze) return;
+
+  const float* src = a.src + shot * a.src_ss;
+  const float* p1 = a.p1 + shot * a.p1_ss;
+  const float* p2 = a.p2 + shot * a.p2_ss;
+  float* out = a.out + shot * a.out_ss;
+  const long long pl = L.plane;
+  // offset of (z = 0, row, column) for this thread's own points and halos
+  const long long colc = (long long)(y + H) * L.px + (x + H) + (long long)H * pl;
+  const long long coly0 = (long long)(y0 - R + ty + H) * L.px + (x + H) + (long long)H * pl;
+  const long long coly1 = (long long)(y0 + T3Y + ty + H) * L.px + (x + H) + (long long)H * pl;
+  const long long colxl = (long long)(y + H) * L.px + (x0 - 4 + H) + (long long)H * pl;
+  const long long colxr = (long long)(y + H) * L.px + (x0 + 4 * T3X + H) + (long long)H * pl;
+  const bool hy = ty < R, hxl = tx == 0, hxr = tx == T3X - 1;
+
+  float4 q[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * R; ++k) q[k] = ld4(src, colc + (long long)(zb - R + k) * pl);
+  float4 nq = ld4(src, colc + (long long)(zb + R) * pl);
+  float4 n1 = ld4(p1, colc + (long long)zb * pl);
+  float4 n2 = ld4(p2, colc + (long long)zb * pl);
+  float4 nh0 = make_float4(0.f, 0.f, 0.f, 0.f), nh1 = nh0, nhx = nh0;
+  if (hy) {
+    nh0 = ld4(src, coly0 + (long long)zb * pl);
+    nh1 = ld4(src, coly1 + (long long)zb * pl);
+  }
+  if (hxl) nhx = ld4(src, colxl + (long long)zb * pl);
+  if (hxr) nhx = ld4(src, colxr + (long long)zb * pl);
+
+  const float w0 = 3.0f * W.w[0];
+  for (int z = zb; z < ze; ++z) {
+    q[2 * R] = nq;
+    // stage plane z (centre from the queue, halo from the prefetch registers)
+    sm[ty + R][tx + 1] = q[R];
+    if (hy) {
+      sm[ty][tx + 1] = nh0;
+      sm[ty + T3Y + R][tx + 1] = nh1;
+    }
+    if (hxl) sm[ty + R][0] = nhx;
+    if (hxr) sm[ty + R][T3X + 1] = nhx;
+    const float4 c1 = n1, c2 = n2;
+    if (z + 1 < ze) {  // prefetch plane z+1 while plane z is computed
+      const long long zo = (long long)(z + 1) * pl;
+      nq = ld4(src, colc + zo + (long long)R * pl);
+      n1 = ld4(p1, colc + zo);
+      n2 = ld4(p2, colc + zo);
+      if (hy) {
+        nh0 = ld4(src, coly0 + zo);
+        nh1 = ld4(src, coly1 + zo);
+      }
+      if (hxl) nhx = ld4(src, colxl + zo);
+      if (hxr) nhx = ld4(src, colxr + zo);
+    }
+    __syncthreads();
+
+    const float4 xl = sm[ty + R][tx], xc = sm[ty + R][tx + 1], xr = sm[ty + R][tx + 2];
+    const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
+    float s[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) s[p] = w0 * v[4 + p];
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+      const float4 yp = sm[ty + R + k][tx + 1], ym = sm[ty + R - k][tx + 1];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const float t = (v[4 + p + k] + v[4 + p - k]) + (comp(yp, p) + comp(ym, p)) +
+                        (comp(q[R + k], p) + comp(q[R - k], p));
+        s[p] = fmaf(W.w[k], t, s[p]);
+      }
+    }
+    float res[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) res[p] = epilogue<MODE>(v[4 + p], s[p], comp(c1, p), comp(c2, p));
+    if (y < L.ny && x < L.nx)
+      store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
+  }
+}
+
+// ------------------------------------------------------------------ 2-D
+constexpr int W2 = 4;  // warps per CTA, each an independent (x strip, z chunk)
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(32 * W2)
+sweep2d(Layout L, Weights W, StencilArgs a, int bz, int nzc, int nxt, int nwarps) {
+  __shared__ float4 sm[W2][32 + 2];
+  const int lane = threadIdx.x, wi = threadIdx.y;
+  const int gw = blockIdx.x * W2 + wi;
+  if (gw >= nwarps) return;
+  const int xt = gw % nxt;
+  const int zc = (gw / nxt) % nzc;
+  const int shot = gw / (nxt * nzc);
+  const int x0 = xt * 128, x = x0 + 4 * lane;
+  const int zb = zc * bz, ze = min(L.nz, zb + bz);
+  if (zb >= ze) return;
+
+  const float* src = a.src + shot * a.src_ss;
+  const float* p1 = a.p1 + shot * a.p1_ss;
+  const float* p2 = a.p2 + shot * a.p2_ss;
+  float* out = a.out + shot * a.out_ss;
+  const long long pl = L.px;  // row pitch (plane == px in 2-D)
+  const long long colc = (long long)(x + H) + (long long)H * pl;
+  const long long colxl = (long long)(x0 - 4 + H) + (long long)H * pl;
+  const long long colxr = (long long)(x0 + 128 + H) + (long long)H * pl;
+  const bool hxl = lane == 0, hxr = lane == 31;
+
+  float4 q[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * R; ++k) q[k] = ld4(src, colc + (long long)(zb - R + k) * pl);
+  float4 nq = ld4(src, colc + (long long)(zb + R) * pl);
+  float4 n1 = ld4(p1, colc + (long long)zb * pl);
+  float4 n2 = ld4(p2, colc + (long long)zb * pl);
+  float4 nhx = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (hxl) nhx = ld4(src, colxl + (long long)zb * pl);
+  if (hxr) nhx = ld4(src, colxr + (long long)zb * pl);
+
+  const float w0 = 2.0f * W.w[0];
+  for (int z = zb; z < ze; ++z) {
+    q[2 * R] = nq;
+    sm[wi][lane + 1] = q[R];
+    if (hxl) sm[wi][0] = nhx;
+    if (hxr) sm[wi][33] = nhx;
+    const float4 c1 = n1, c2 = n2;
+    if (z + 1 < ze) {
+      const long long zo = (long long)(z + 1) * pl;
+      nq = ld4(src, colc + zo + (long long)R * pl);
+      n1 = ld4(p1, colc + zo);
+      n2 = ld4(p2, colc + zo);
+      if (hxl) nhx = ld4(src, colxl + zo);
+      if (hxr) nhx = ld4(src, colxr + zo);
+    }
+    __syncwarp();
+    const float4 xl = sm[wi][lane], xc = sm[wi][lane + 1], xr = sm[wi][lane + 2];
+    const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
+    float res[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float c = v[4 + p];
+      float s = w0 * c;
+#pragma unroll
+      for (int k = 1; k <= R; ++k) {
+        const float t = (v[4 + p + k] + v[4 + p - k]) + (comp(q[R + k], p) + comp(q[R - k], p));
+        s = fmaf(W.w[k], t, s);
+      }
+      res[p] = epilogue<MODE>(c, s, comp(c1, p), comp(c2, p));
+    }
+    if (x < L.nx) store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
+  }
+}
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+template <int R, int MODE>
+cudaError_t launch3d(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s) {
+  static int occ = 0;
+  if (occ == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep3d<R, MODE>, T3X * T3Y, 0);
+    if (occ <= 0) occ = 1;
+  }
+  const int gx = (L.nx + 4 * T3X - 1) / (4 * T3X), gy = (L.ny + T3Y - 1) / T3Y;
+  const long long tiles = (long long)gx * gy * a.nshots;
+  const long long target = 2LL * occ * num_sms();
+  int nzc = (int)std::max<long long>(1, (target + tiles - 1) / tiles);
+  nzc = std::min(nzc, std::max(1, L.nz / 8));
+  const int bz = (L.nz + nzc - 1) / nzc;
+  nzc = (L.nz + bz - 1) / bz;
+  dim3 grid(gx, gy, nzc * a.nshots), block(T3X, T3Y);
+  sweep3d<R, MODE><<<grid, block, 0, s>>>(L, W, a, bz, nzc);
+  return cudaGetLastError();
+}
+
+template <int R, int MODE>
+cudaError_t launch2d(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s) {
+  const int nxt = (L.nx + 127) / 128;
+  const long long strips = (long long)nxt * a.nshots;
+  const long long target = 16LL * W2 * num_sms();  // warps
+  int nzc = (int)std::max<long long>(1, (target + strips - 1) / strips);
+  nzc = std::min(nzc, std::max(1, L.nz / 8));
+  const int bz = (L.nz + nzc - 1) / nzc;
+  nzc = (L.nz + bz - 1) / bz;
+  const int nwarps = nxt * nzc * a.nshots;
+  dim3 grid((nwarps + W2 - 1) / W2), block(32, W2);
+  sweep2d<R, MODE><<<grid, block, 0, s>>>(L, W, a, bz, nzc, nxt, nwarps);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& a,
+                           cudaStream_t s) {
+  const int kind = mode == MODE_STEP ? 0 : 1;  // TP_KERNEL_STENCIL / TP_KERNEL_IMAGING
+  prof_before(kind, s);
+  cudaError_t e;
+  if (L.ndim == 3) {
+    if (W.R == 4) e = mode == MODE_STEP ? launch3d<4, MODE_STEP>(L, W, a, s) : launch3d<4, MODE_IMAGE>(L, W, a, s);
+    else e = mode == MODE_STEP ? launch3d<2, MODE_STEP>(L, W, a, s) : launch3d<2, MODE_IMAGE>(L, W, a, s);
+  } else {
+    if (W.R == 4) e = mode == MODE_STEP ? launch2d<4, MODE_STEP>(L, W, a, s) : launch2d<4, MODE_IMAGE>(L, W, a, s);
+    else e = mode == MODE_STEP ? launch2d<2, MODE_STEP>(L, W, a, s) : launch2d<2, MODE_IMAGE>(L, W, a, s);
+  }
+  prof_after(kind, s);
+  return e;
+}
+
+}  // namespace tp

@@ -1,0 +1,122 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point that include/tprobe.h declares; host-only logic
+(argument validation, workspace sizes, memory model) behaves as documented.
+No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2104_00794_gb300 import build, native
+from paper_2104_00794_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def L():
+    return native.lib()
+
+
+def _grid(w, nt=None, vmax=0.0):
+    return native.tp_grid(w.ndim, w.nx, w.ny, w.nz, w.h, w.dt, w.nt if nt is None else nt, w.order, vmax)
+
+
+def _geom(w, fake_ptr=0x1000):
+    return native.tp_geom(w.nshots, w.nsrc, fake_ptr, w.nrec, fake_ptr)
+
+
+def test_library_exports_every_declared_symbol(L):
+    declared = native.exported_symbols()
+    assert {"tp_forward", "tp_adjoint", "tp_gradient_probed", "tp_gradient_full",
+            "tp_workspace_bytes"} <= set(declared)
+    for name in declared:
+        assert hasattr(L, name), name
+    # the library is built for sm_103a only
+    objdir = os.path.join(build.LIBDIR, "obj")
+    assert os.path.exists(build.LIB)
+    assert set(os.listdir(objdir)) >= {s.replace(".cu", ".o") for s in build.SOURCES}
+
+
+def test_header_declares_extern_c_and_cites_the_paper():
+    with open(os.path.join(build.INCLUDE, "tprobe.h")) as f:
+        text = f.read()
+    assert 'extern "C"' in text
+    for cite in ("Algorithm 1", "Eq. 2", "Eq. 3", "Eq. 4"):
+        assert cite in text
+
+
+def test_workspace_sizes_follow_the_memory_model(L):
+    w = wl.config3()
+    g, geo = _grid(w), _geom(w)
+    pr = native.tp_probe(0, 32, 32, 1, None, 0.0)
+    full = native.tp_workspace_bytes(native.OP_GRADIENT_FULL, g, geo)
+    probed = native.tp_workspace_bytes(native.OP_GRADIENT_PROBED, g, geo, pr)
+    N, nt = w.N, w.nt
+    # full storage holds the N x nt history (padded layout adds < 12 %)
+    assert 4 * N * nt <= full <= 1.12 * 4 * N * nt + 2 * 4 * w.nt * w.nrec + (1 << 30)
+    # probed: 2 N r accumulators + (T + 2) ring levels (+ padding), >= 10x less
+    assert probed >= 4 * N * (2 * 32 + 34)
+    assert full / probed >= 10.0
+    # window 64 costs 32 more ring levels
+    pr64 = native.tp_probe(0, 32, 64, 1, None, 0.0)
+    p64 = native.tp_workspace_bytes(native.OP_GRADIENT_PROBED, g, geo, pr64)
+    assert p64 > probed
+    # forward/adjoint need three levels only
+    fwd = native.tp_workspace_bytes(native.OP_FORWARD, g, geo)
+    assert fwd < probed / 10
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda g, p: setattr(g, "ndim", 4), "ndim"),
+    (lambda g, p: setattr(g, "order", 6), "order"),
+    (lambda g, p: setattr(g, "nt", 2), "nt"),
+    (lambda g, p: setattr(g, "ny", 3), "ny"),
+    (lambda g, p: setattr(g, "h", -1.0), "positive"),
+    (lambda g, p: setattr(p, "r", 0), "r must"),
+    (lambda g, p: setattr(p, "r", 300), "r must"),
+    (lambda g, p: setattr(p, "T", 48), "window"),
+    (lambda g, p: setattr(p, "kind", 2), "identity"),
+    (lambda g, p: setattr(p, "kind", 3), "Z_user"),
+    (lambda g, p: setattr(p, "kind", 9), "kind"),
+])
+def test_invalid_arguments_are_rejected(L, mutate, msg):
+    w = wl.small_2d()
+    g, geo = _grid(w), _geom(w)
+    pr = native.tp_probe(0, 4, 32, 1, None, 0.0)
+    mutate(g, pr)
+    n = L.tp_workspace_bytes(native.OP_GRADIENT_PROBED, ctypes.byref(g), ctypes.byref(geo), ctypes.byref(pr))
+    assert n == 0
+    assert msg in native.last_error()
+
+
+def test_null_geometry_and_counts_rejected(L):
+    w = wl.small_2d()
+    g = _grid(w)
+    geo = native.tp_geom(1, 1, None, 3, 0x1000)
+    assert L.tp_workspace_bytes(native.OP_FORWARD, ctypes.byref(g), ctypes.byref(geo), None) == 0
+    geo = native.tp_geom(0, 1, 0x1000, 3, 0x1000)
+    assert L.tp_workspace_bytes(native.OP_FORWARD, ctypes.byref(g), ctypes.byref(geo), None) == 0
+    # a call with a NULL workspace fails before touching the device
+    geo = _geom(w)
+    st = L.tp_forward(ctypes.byref(g), ctypes.byref(geo), 0x1000, 0x1000, 0x1000, None, 0, None)
+    assert st == native.TP_ERR_ARG
+    st = L.tp_forward(ctypes.byref(g), ctypes.byref(geo), 0x1000, 0x1000, 0x1000, 0x1000, 16, None)
+    assert st == native.TP_ERR_NOMEM and "needed" in native.last_error()
+
+
+def test_kernel_names(L):
+    names = [L.tp_kernel_name(k).decode() for k in range(native.KERNEL_KINDS)]
+    assert names[0] == "stencil_step" and "probe_gemm_tcgen05" in names
+    assert L.tp_kernel_name(99).decode() == "unknown"
+
+
+def test_no_cpu_fallback_in_product_path():
+    """The product package never imports the checker."""
+    pkg = os.path.dirname(native.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                with open(os.path.join(root, f)) as fh:
+                    src = fh.read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", src, re.M), f
+                assert "tp_oracle" not in src, f

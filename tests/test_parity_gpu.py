@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.
+
+Tolerances (stated by the hot-path contract, derived for fp32 arithmetic):
+  * traces of F and F^T: relative L2 <= 1e-5 (fp32 leapfrog over <= 500
+    steps accumulates a few 1e-7 per step of relative rounding);
+  * gradients (full storage and probed with the same probes): relative L2
+    <= 1e-4 (products of two fp32 wavefields summed over nt levels);
+  * probes: bit-exact (integer hash, exactly representable values);
+  * fp64 misfit: relative 1e-5 (inherits the fp32 trace error).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_00794_gb300 import api, native
+from paper_2104_00794_gb300 import workloads as wl
+from parity_util import host, oracle_dobs, problem, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TRACE_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(autouse=True)
+def _lib(cuda_lib):
+    yield
+
+
+CASES_2D = [
+    dict(nx=300, nz=70, nt=220, order=8, nshots=2),    # 3 x-strips, ragged tail
+    dict(nx=67, nz=45, nt=160, order=4, nshots=1),
+    dict(nx=129, nz=9, nt=90, order=8, nshots=3),      # one strip + 1 column
+]
+CASES_3D = [
+    dict(nx=70, ny=37, nz=45, nt=90, order=8, nshots=2),  # 2 x-tiles, 3 y-tiles, ragged
+    dict(nx=36, ny=22, nz=28, nt=80, order=4, nshots=1),
+]
+
+
+def _w(case, **kw):
+    c = dict(case)
+    c.update(kw)
+    if "ny" in c:
+        return wl.small_3d(**c)
+    return wl.small_2d(**c)
+
+
+# ------------------------------------------------------------------ probes
+@pytest.mark.parametrize("kind,nt,r", [("rademacher", 500, 4), ("gaussian", 3000, 16), ("rademacher", 2000, 32),
+                                       ("gaussian", 77, 5), ("identity", 64, 64)])
+def test_probes_bit_exact(kind, nt, r):
+    p = api.Problem(2, 8, 1, 8, 10.0, 1e-3, nt, 4, [[1]], [[2]], vmax=1500.0)
+    for shot in (0, 3):
+        spec = api.ProbeSpec(kind=kind, r=r, seed=2104 + shot)
+        Z = host(p.probes(spec, shot))
+        ref = oracle.probes(kind, nt, r, 2104 + shot, shot)
+        assert np.array_equal(Z.astype(np.float64), ref)
+
+
+# ------------------------------------------------------------------ F and F^T
+@pytest.mark.parametrize("case", CASES_2D + CASES_3D, ids=lambda c: "x".join(str(c[k]) for k in ("nz", "ny", "nx") if k in c) + f"_o{c['order']}")
+def test_forward_traces(case):
+    w = _w(case)
+    p = problem(w)
+    d = host(p.forward(to_dev(w.vel_true), to_dev(w.wavelet)))
+    ref = oracle.batch_forward(w, w.vel_true)
+    assert d.shape == ref.shape
+    assert np.all(d[:, :2] == 0.0)
+    assert rel_l2(d, ref) <= TRACE_TOL, rel_l2(d, ref)
+    for s in range(w.nshots):
+        assert rel_l2(d[s], ref[s]) <= TRACE_TOL
+
+
+@pytest.mark.parametrize("case", [CASES_2D[0], CASES_3D[0]], ids=["2d", "3d"])
+def test_adjoint_traces_and_dot_product(case):
+    w = _w(case)
+    p = problem(w)
+    rng = np.random.default_rng(3)
+    s = rng.standard_normal((w.nshots, w.nt, w.nrec)).astype(np.float32)
+    q = rng.standard_normal((w.nshots, w.nt, w.nsrc)).astype(np.float32)
+    vel = to_dev(w.vel_true)
+    qa = host(p.adjoint(vel, to_dev(s)))
+    g = oracle.grid_of(w)
+    ref = np.stack([oracle.adjoint(g, w.src[i], w.rec[i], w.vel_true, s[i]) for i in range(w.nshots)])
+    assert rel_l2(qa, ref) <= TRACE_TOL
+    assert np.all(qa[:, 0] == 0.0) and np.all(qa[:, -1] == 0.0)
+    fq = host(p.forward(vel, to_dev(q)))
+    lhs = float(np.sum(fq.astype(np.float64) * s))
+    rhs = float(np.sum(q.astype(np.float64) * qa))
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
+
+
+# ------------------------------------------------------------------ gradients
+@pytest.mark.parametrize("case", [CASES_2D[0], CASES_2D[1], CASES_3D[0]], ids=["2d_o8", "2d_o4", "3d_o8"])
+def test_full_gradient(case):
+    w = _w(case)
+    p = problem(w)
+    dobs = oracle_dobs(w)
+    grad, sc = p.gradient_full(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs))
+    grad, sc = host(grad), host(sc)
+    ref, J = oracle.batch_gradient_full(w, w.vel0, dobs)
+    assert rel_l2(grad, ref) <= GRAD_TOL, rel_l2(grad, ref)
+    assert sc[0] == pytest.approx(J, rel=1e-5)
+    assert sc[1] == pytest.approx(np.linalg.norm(grad.astype(np.float64)), rel=1e-6)
+
+
+@pytest.mark.parametrize("case,kind,r,T", [
+    (CASES_2D[0], "rademacher", 4, 32),
+    (CASES_2D[0], "gaussian", 16, 64),
+    (CASES_2D[1], "gaussian", 5, 32),
+    (CASES_2D[2], "rademacher", 32, 32),
+    (CASES_3D[0], "rademacher", 8, 32),
+    (CASES_3D[1], "gaussian", 16, 64),
+], ids=["2d_rad4", "2d_gau16_T64", "2d_o4_gau5", "2d_3shots_r32", "3d_rad8", "3d_o4_gau16_T64"])
+def test_probed_gradient_same_probes(case, kind, r, T):
+    w = _w(case, r=r, probe_kind=kind, T=T)
+    p = problem(w)
+    dobs = oracle_dobs(w)
+    spec = api.ProbeSpec(kind=kind, r=r, T=T, seed=w.seed)
+    grad, sc = p.gradient_probed(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs), spec)
+    grad, sc = host(grad), host(sc)
+    ref, J = oracle.batch_gradient_probed(w, w.vel0, dobs, kind=kind, r=r, seed=w.seed)
+    assert rel_l2(grad, ref) <= GRAD_TOL, rel_l2(grad, ref)
+    assert sc[0] == pytest.approx(J, rel=1e-5)
+    assert sc[1] == pytest.approx(np.linalg.norm(grad.astype(np.float64)), rel=1e-6)
+    p.status(native.OP_GRADIENT_PROBED)
+
+
+def test_identity_probes_reproduce_full_gradient():
+    """Q = I (r = nt): the probed path computes Eq. 3 exactly (to rounding)."""
+    w = _w(CASES_2D[1], nt=96)
+    p = problem(w)
+    dobs = oracle_dobs(w)
+    args = (to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs))
+    gp, _ = p.gradient_probed(*args, api.ProbeSpec(kind="identity", r=w.nt, T=32))
+    gf, _ = p.gradient_full(*args)
+    ref, _ = oracle.batch_gradient_full(w, w.vel0, dobs)
+    assert rel_l2(host(gp), host(gf)) <= 1e-5
+    assert rel_l2(host(gp), ref) <= GRAD_TOL
+
+
+# ------------------------------------------------------------------ edge cases
+def test_minimum_nt_gives_zero_gradient():
+    w = _w(CASES_2D[1], nt=3)
+    p = problem(w)
+    dobs = np.zeros((1, 3, w.nrec), np.float32)
+    g, sc = p.gradient_probed(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs), api.ProbeSpec(r=4))
+    assert np.all(host(g) == 0.0) and host(sc)[0] == 0.0
+    g, sc = p.gradient_full(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs))
+    assert np.all(host(g) == 0.0)
+
+
+def test_tiny_grid_and_coincident_points():
+    """A 5 x 3 grid, source at a corner, a receiver on the source node."""
+    nx, nz, nt = 5, 3, 40
+    vel = np.full((nz, nx), 1500.0, np.float32)
+    src = np.array([[0]])
+    rec = np.array([[0, 4, 14]])
+    wav = wl.ricker(nt, 1e-3, 30.0).astype(np.float32)[None, :, None]
+    p = api.Problem(2, nx, 1, nz, 10.0, 1e-3, nt, 8, src, rec, vmax=1500.0)
+    d = host(p.forward(to_dev(vel), to_dev(wav)))
+    g = oracle.make_grid(2, nx, 1, nz, 10.0, 1e-3, nt, 8)
+    ref = oracle.forward(g, src[0], rec[0], vel, wav[0])
+    assert rel_l2(d[0], ref) <= TRACE_TOL
+
+
+def test_errors_are_reported():
+    w = _w(CASES_2D[1])
+    p = problem(w)
+    vel = to_dev(w.vel0)
+    with pytest.raises(native.TprobeError) as e:   # CFL violation
+        bad = api.Problem(2, w.nx, 1, w.nz, w.h, 0.01, w.nt, w.order, w.src, w.rec)
+        bad.forward(vel, to_dev(w.wavelet))
+    assert e.value.status == native.TP_ERR_UNSTABLE
+    with pytest.raises(native.TprobeError) as e:   # receiver outside the grid (checked with vmax = 0)
+        bad = api.Problem(2, w.nx, 1, w.nz, w.h, w.dt, w.nt, w.order, w.src, np.array([[0, w.N + 5]]))
+        bad.forward(vel, to_dev(w.wavelet))
+    assert e.value.status == native.TP_ERR_ARG
+    with pytest.raises(native.TprobeError) as e:   # workspace too small
+        native.tp_forward(p.grid, p.geom, vel.data_ptr(), vel.data_ptr(), vel.data_ptr(), vel.data_ptr(), 256,
+                          torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == native.TP_ERR_NOMEM
+
+
+# ------------------------------------------------------------------ full-size grid
+@pytest.mark.slow
+def test_full_size_3d_grid_truncated_time():
+    """The 256^3 bench grid in the bench's launch configuration, with nt cut
+    to 48 so that the oracle finishes: traces and the probed gradient."""
+    w = wl.config3(nt=48)
+    p = problem(w)
+    dobs = wl.synthetic_data(1, w.nt, w.nrec, seed=5)
+    d = host(p.forward(to_dev(w.vel_true), to_dev(w.wavelet)))
+    ref = oracle.batch_forward(w, w.vel_true)
+    assert rel_l2(d, ref) <= TRACE_TOL
+    spec = api.ProbeSpec(kind="rademacher", r=32, T=32, seed=w.seed)
+    grad, _ = p.gradient_probed(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs), spec)
+    gref, _ = oracle.batch_gradient_probed(w, w.vel0, dobs)
+    assert rel_l2(host(grad), gref) <= GRAD_TOL
