@@ -259,8 +259,10 @@ def small_3d(nx=36, ny=22, nz=28, nt=90, order=8, nshots=1, r=4, probe_kind="rad
     vclip = 0.8 * CFL_LIMIT[(3, order)] * h / dt
     vt = np.minimum(layered_3d(0, seed, nlayers=4, vmin=1500.0, vmax=3000.0,
                                blob_sigma=4.0, shape=(nz, ny, nx)), vclip).astype(np.float32)
-    v0 = np.minimum(layered_3d(0, seed, nlayers=4, vmin=1500.0, vmax=3000.0, with_blob=False,
-                               shape=(nz, ny, nx)), vclip).astype(np.float32)
+    # background 5 % slow everywhere, so the residual is a physical signal from
+    # the first arrival on (not only the anomaly's late reflection)
+    v0 = (0.95 * np.minimum(layered_3d(0, seed, nlayers=4, vmin=1500.0, vmax=3000.0, with_blob=False,
+                                       shape=(nz, ny, nx)), vclip)).astype(np.float32)
     pos = np.round(np.linspace(0, nx - 1, nshots + 2)[1:-1]).astype(np.int64)
     src = flat_index(nx, ny, 3, ny // 2, pos).reshape(nshots, 1)
     rec = surface_receivers_3d(nx, ny, row=1, stride=rec_stride)

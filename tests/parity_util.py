@@ -25,7 +25,7 @@ def oracle_dobs(w, nt=None):
 
 
 def to_dev(a):
-    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    return torch.as_tensor(np.array(a, copy=True, order="C"), device="cuda")
 
 
 def host(t):
