@@ -231,6 +231,14 @@ double cfl_limit(const Plan& P) {
   return 2.0 / std::sqrt(P.L.ndim * std::fabs(sym));
 }
 
+// A family of padded fields in the workspace: `nfields` consecutive fields at
+// byte offset `off`, shot s's copy of field f at index f + s * fs.
+struct Fam {
+  size_t off;
+  int nfields;
+  int fs;
+};
+
 struct Ctx {
   const Plan& P;
   char* ws;
@@ -239,6 +247,9 @@ struct Ctx {
   Scal* scal() const { return at<Scal>(P.o_scal); }
   int* err() const { return &scal()->err; }
   float* field(size_t base, long long i) const { return at<float>(base) + i * P.L.field; }
+  float* ptr(const Fam& f, int f0) const { return field(f.off, f0); }
+  long long ss(const Fam& f) const { return (long long)f.fs * P.L.field; }
+  FieldRef ref(const Fam& f, int f0) const { return FieldRef{at<float>(f.off), f.nfields, f0, f.fs}; }
 };
 
 tp_status check_ws(const Plan& P, void* ws, size_t ws_bytes) {
@@ -276,9 +287,9 @@ tp_status setup(const Ctx& c, const tp_grid* g, const tp_geom* geo, const float*
   return TP_OK;
 }
 
-tp_status step(const Ctx& c, const float* cur, const float* old, float* out, long long ss) {
-  StencilArgs a{cur, ss, old, ss, c.at<float>(c.P.o_c2), 0, out, ss, c.P.nshots};
-  TRY(launch_stencil(MODE_STEP, c.P.L, c.P.W, a, c.st));
+tp_status step(const Ctx& c, const Fam& f, int cur, int old, int out) {
+  StencilArgs a{c.ref(f, cur), c.ref(f, old), c.ref(Fam{c.P.o_c2, 1, 0}, 0), c.ptr(f, out), c.ss(f), c.P.nshots};
+  TRY(launch_stencil(MODE_STEP, c.P.L, c.P.W, a, c.st, c.err()));
   return TP_OK;
 }
 
@@ -304,23 +315,23 @@ tp_status point(const Ctx& c, const float* samp, long long samp_ss, const long l
     if (s_ != TP_OK) return s_;       \
   } while (0)
 
-// Forward loop (Algorithm 1 lines 0-3).  level(t) gives the shot-0 field of
-// level t; `ss` is the shot stride.  d (may be null) receives R u[t];
+// Forward loop (Algorithm 1 lines 0-3).  Level t of every shot lives in
+// field level(t) of family f.  d (may be null) receives R u[t];
 // after_level(t) runs once level t is complete (sources injected).
 template <class LevelFn, class AfterFn>
-tp_status forward_loop(const Ctx& c, LevelFn level, long long ss, const float* wav, float* d, AfterFn after_level) {
+tp_status forward_loop(const Ctx& c, const Fam& f, LevelFn level, const float* wav, float* d, AfterFn after_level) {
   const Plan& P = c.P;
-  const long long dss = (long long)P.nt * P.nrec, wss = (long long)P.nt * P.nsrc;
+  const long long dss = (long long)P.nt * P.nrec, wss = (long long)P.nt * P.nsrc, ss = c.ss(f);
   for (int t = 1; t <= P.nt - 2; ++t) {
-    TRYS(step(c, level(t), level(t - 1), level(t + 1), ss));
-    TRYS(point(c, d ? level(t) : nullptr, ss, c.at<long long>(P.o_roff), P.nrec, d ? d + (long long)t * P.nrec : nullptr,
-               dss, level(t + 1), ss, c.at<long long>(P.o_soff), c.at<float>(P.o_cs), P.nsrc,
-               wav + (long long)t * P.nsrc, wss));
+    TRYS(step(c, f, level(t), level(t - 1), level(t + 1)));
+    TRYS(point(c, d ? c.ptr(f, level(t)) : nullptr, ss, c.at<long long>(P.o_roff), P.nrec,
+               d ? d + (long long)t * P.nrec : nullptr, dss, c.ptr(f, level(t + 1)), ss, c.at<long long>(P.o_soff),
+               c.at<float>(P.o_cs), P.nsrc, wav + (long long)t * P.nsrc, wss));
     TRYS(after_level(t + 1));
   }
   if (d)
-    TRYS(point(c, level(P.nt - 1), ss, c.at<long long>(P.o_roff), P.nrec, d + (long long)(P.nt - 1) * P.nrec, dss,
-               nullptr, 0, nullptr, nullptr, 0, nullptr, 0));
+    TRYS(point(c, c.ptr(f, level(P.nt - 1)), ss, c.at<long long>(P.o_roff), P.nrec, d + (long long)(P.nt - 1) * P.nrec,
+               dss, nullptr, 0, nullptr, nullptr, 0, nullptr, 0));
   return TP_OK;
 }
 
@@ -328,22 +339,22 @@ tp_status forward_loop(const Ctx& c, LevelFn level, long long ss, const float* w
 // q_out (may be null) receives S lambda[t+1] at row t; acc/aval accumulate
 // sum_k lambda[k][src] q[k-1] for the full gradient's source term.
 template <class LevelFn, class AfterFn>
-tp_status adjoint_loop(const Ctx& c, LevelFn level, long long ss, const float* s, float* q_out, double* acc,
+tp_status adjoint_loop(const Ctx& c, const Fam& f, LevelFn level, const float* s, float* q_out, double* acc,
                        const float* aval, AfterFn after_level) {
   const Plan& P = c.P;
-  const long long sss = (long long)P.nt * P.nrec, qss = (long long)P.nt * P.nsrc;
+  const long long sss = (long long)P.nt * P.nrec, qss = (long long)P.nt * P.nsrc, ss = c.ss(f);
   const bool samp = q_out || acc;
   for (int j = P.nt - 1; j >= 2; --j) {
-    TRYS(step(c, level(j + 1), level(j + 2), level(j), ss));
-    TRYS(point(c, samp ? level(j + 1) : nullptr, ss, c.at<long long>(P.o_soff), P.nsrc,
-               q_out ? q_out + (long long)j * P.nsrc : nullptr, qss, level(j), ss, c.at<long long>(P.o_roff),
+    TRYS(step(c, f, level(j + 1), level(j + 2), level(j)));
+    TRYS(point(c, samp ? c.ptr(f, level(j + 1)) : nullptr, ss, c.at<long long>(P.o_soff), P.nsrc,
+               q_out ? q_out + (long long)j * P.nsrc : nullptr, qss, c.ptr(f, level(j)), ss, c.at<long long>(P.o_roff),
                c.at<float>(P.o_cr), P.nrec, s + (long long)j * P.nrec, sss, acc,
                aval ? aval + (long long)j * P.nsrc : nullptr, qss));
     TRYS(after_level(j));
   }
   if (samp)
-    TRYS(point(c, level(2), ss, c.at<long long>(P.o_soff), P.nsrc, q_out ? q_out + P.nsrc : nullptr, qss, nullptr, 0,
-               nullptr, nullptr, 0, nullptr, 0, acc, aval ? aval + P.nsrc : nullptr, qss));
+    TRYS(point(c, c.ptr(f, level(2)), ss, c.at<long long>(P.o_soff), P.nsrc, q_out ? q_out + P.nsrc : nullptr, qss,
+               nullptr, 0, nullptr, nullptr, 0, nullptr, 0, acc, aval ? aval + P.nsrc : nullptr, qss));
   return TP_OK;
 }
 
@@ -387,9 +398,9 @@ tp_status tp_forward(const tp_grid* grid, const tp_geom* geom, const float* vel,
   TRYS(setup(c, grid, geom, vel));
   TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * P.L.field * sizeof(float), c.st));
   TRY(cudaMemsetAsync(d_out, 0, (size_t)P.nshots * P.nt * P.nrec * sizeof(float), c.st));
-  const long long ss = 3 * P.L.field;
-  auto level = [&](int t) { return c.field(P.o_f, t % 3); };
-  TRYS(forward_loop(c, level, ss, wavelet, d_out, [](int) { return TP_OK; }));
+  const Fam f{P.o_f, (int)P.nf, 3};
+  auto level = [](int t) { return t % 3; };
+  TRYS(forward_loop(c, f, level, wavelet, d_out, [](int) { return TP_OK; }));
   return TP_OK;
 }
 
@@ -403,9 +414,9 @@ tp_status tp_adjoint(const tp_grid* grid, const tp_geom* geom, const float* vel,
   TRYS(setup(c, grid, geom, vel));
   TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * P.L.field * sizeof(float), c.st));
   TRY(cudaMemsetAsync(q_out, 0, (size_t)P.nshots * P.nt * P.nsrc * sizeof(float), c.st));
-  const long long ss = 3 * P.L.field;
-  auto level = [&](int t) { return c.field(P.o_f, t % 3); };
-  TRYS(adjoint_loop(c, level, ss, d_in, q_out, nullptr, nullptr, [](int) { return TP_OK; }));
+  const Fam f{P.o_f, (int)P.nf, 3};
+  auto level = [](int t) { return t % 3; };
+  TRYS(adjoint_loop(c, f, level, d_in, q_out, nullptr, nullptr, [](int) { return TP_OK; }));
   return TP_OK;
 }
 
@@ -429,7 +440,8 @@ tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_
   TRY(cudaMemsetAsync(d, 0, (size_t)P.nshots * nt * P.nrec * sizeof(float), c.st));
   float* Q = c.at<float>(P.o_Q);
   TRY(launch_probes(P.kind, nt, r, probe->seed, 0, P.nshots, probe->Z_user, Q, c.st));
-  auto level = [&](int t) { return c.field(P.o_f, t % S); };
+  const Fam ring{P.o_f, (int)P.nf, S};
+  auto level = [S](int t) { return t % S; };
 
   GemmArgs g{};
   g.ring = c.at<float>(P.o_f); g.slot_stride = P.L.field; g.ring_ss = ring_ss; g.nslots = S;
@@ -451,13 +463,13 @@ tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_
     }
     return TP_OK;
   };
-  TRYS(forward_loop(c, level, ring_ss, wavelet, d, fwd_after));
+  TRYS(forward_loop(c, ring, level, wavelet, d, fwd_after));
   TRYS(misfit_and_residual(c, d, d_obs, misfit));
 
   // adjoint: V_s[:, i] = sum_{k=2}^{nt-1} Q_s[k, i] lambda_s[k]  (windows from the top)
   for (int k = nt; k <= nt + 1; ++k)
     for (int s = 0; s < P.nshots; ++s)
-      TRY(cudaMemsetAsync(level(k) + s * ring_ss, 0, fb, c.st));
+      TRY(cudaMemsetAsync(c.ptr(ring, level(k)) + s * ring_ss, 0, fb, c.st));
   g.P = c.at<float>(P.o_V); g.qshift = 0;
   auto adj_after = [&](int lev) -> tp_status {
     const int top = nt - 1 - ((nt - 1 - lev) / T) * T;
@@ -469,14 +481,14 @@ tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_
     }
     return TP_OK;
   };
-  TRYS(adjoint_loop(c, level, ring_ss, d, nullptr, nullptr, nullptr, adj_after));
+  TRYS(adjoint_loop(c, ring, level, d, nullptr, nullptr, nullptr, adj_after));
 
   // combine (Algorithm 1 line 8): ubar = v^2 (L P + S^T qbar), grad = -scale sum_i ubar vbar
   const long long pss = (long long)r * P.L.field;
+  const Fam fP{P.o_P, (int)(P.nshots * r), r}, fV{P.o_V, (int)(P.nshots * r), r}, fG{P.o_gacc, P.nshots, 1};
   for (int i = 0; i < r; ++i) {
-    StencilArgs a{c.field(P.o_P, i), pss, c.field(P.o_V, i), pss, c.at<float>(P.o_gacc), P.L.field,
-                  c.at<float>(P.o_gacc), P.L.field, P.nshots};
-    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st));
+    StencilArgs a{c.ref(fP, i), c.ref(fV, i), c.ref(fG, 0), c.ptr(fG, 0), c.ss(fG), P.nshots};
+    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
   }
   TRY(launch_finish_grad(P.L, vel, c.at<float>(P.o_gacc), P.nshots, P.L.field, P.scale / (grid->h * grid->h), grad,
                          c.st));
@@ -498,26 +510,25 @@ tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float
   TRYS(setup(c, grid, geom, vel));
   const size_t fb = (size_t)P.L.field * sizeof(float);
   const int nt = P.nt;
-  const long long hist_ss = (long long)nt * P.L.field, lam_ss = 3 * P.L.field;
   TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));
   TRY(cudaMemsetAsync(c.at<float>(P.o_P), 0, (size_t)3 * P.nshots * fb, c.st));
   TRY(cudaMemsetAsync(c.at<float>(P.o_gacc), 0, (size_t)P.nshots * fb, c.st));
   TRY(cudaMemsetAsync(c.at<double>(P.o_sacc), 0, (size_t)P.nshots * P.nsrc * sizeof(double), c.st));
   float* d = c.at<float>(P.o_d);
   TRY(cudaMemsetAsync(d, 0, (size_t)P.nshots * nt * P.nrec * sizeof(float), c.st));
-  auto hist = [&](int t) { return c.field(P.o_f, t); };
-  TRYS(forward_loop(c, hist, hist_ss, wavelet, d, [](int) { return TP_OK; }));
+  const Fam fh{P.o_f, (int)P.nf, nt}, fl{P.o_P, 3 * P.nshots, 3}, fG{P.o_gacc, P.nshots, 1};
+  auto hist = [](int t) { return t; };
+  TRYS(forward_loop(c, fh, hist, wavelet, d, [](int) { return TP_OK; }));
   TRYS(misfit_and_residual(c, d, d_obs, misfit));
   // adjoint with the imaging condition of Eq. 3 in its stencil form:
   // gacc_s += lambda_s[j] * S(u_s[j-1])   (udd[j] = v^2 (L u[j-1] + S^T q[j-1]))
-  auto lam = [&](int k) { return c.field(P.o_P, k % 3); };
+  auto lam = [](int k) { return k % 3; };
   auto imaging = [&](int j) -> tp_status {
-    StencilArgs a{hist(j - 1), hist_ss, lam(j), lam_ss, c.at<float>(P.o_gacc), P.L.field, c.at<float>(P.o_gacc),
-                  P.L.field, P.nshots};
-    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st));
+    StencilArgs a{c.ref(fh, j - 1), c.ref(fl, lam(j)), c.ref(fG, 0), c.ptr(fG, 0), c.ss(fG), P.nshots};
+    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
     return TP_OK;
   };
-  TRYS(adjoint_loop(c, lam, lam_ss, d, nullptr, c.at<double>(P.o_sacc), wavelet, imaging));
+  TRYS(adjoint_loop(c, fl, lam, d, nullptr, c.at<double>(P.o_sacc), wavelet, imaging));
   TRY(launch_finish_grad(P.L, vel, c.at<float>(P.o_gacc), P.nshots, P.L.field, 1.0f / (grid->h * grid->h), grad,
                          c.st));
   TRY(launch_source_term(P.L, vel, geom->src, c.at<long long>(P.o_soff), P.nsrc, P.nshots, 1.0f, nullptr, nullptr, 0,

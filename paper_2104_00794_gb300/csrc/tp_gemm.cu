@@ -100,8 +100,11 @@ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int KP) {
   return (uint32_t)((((row >> 3) * (KP >> 2) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
 }
 
-template <int KP>
-__global__ void __launch_bounds__(TILE_M, 1)
+// KP: padded window length (K); PC: probe columns whose old accumulator
+// values are prefetched in registers together with the snapshots (r <= PC),
+// 0 selects the chunked epilogue for large r.
+template <int KP, int PC>
+__global__ void __launch_bounds__(TILE_M)
 probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // layout: A_hi | A_lo | B_hi | B_lo | mbarrier | tmem slot
@@ -113,7 +116,7 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
   uint64_t* mbar = reinterpret_cast<uint64_t*>(B_lo + b_bytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int shot = blockIdx.y;
   const float* ring = a.ring + shot * a.ring_ss;
   const float* Q = a.Q + shot * a.q_ss;
@@ -138,6 +141,9 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
     *reinterpret_cast<float*>(B_hi + kmaj_off(n, k, KP)) = hi;
     *reinterpret_cast<float*>(B_lo + kmaj_off(n, k, KP)) = v - hi;
   }
+  // ring slot of the window's first level; the window (<= KP < nslots
+  // levels) wraps around the ring at most once
+  const int slot0 = a.level0 % a.nslots;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -152,26 +158,30 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
   bool ok = true;
   uint32_t phase = 0;
 
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const long long m0 = tile * TILE_M;
-    const long long pt = m0 + tid;
+  // register prefetch of one tile: the snapshots (A) and the old accumulators
+  float av[KP];
+  float pv[PC > 0 ? PC : 1];
+  auto load_tile = [&](long long tile) {
+    const long long pt = tile * TILE_M + tid;
     const bool in = pt < a.M;
-    // 1. stage A: row = this thread's point, K = the window's levels.  All
-    //    KP loads are issued before any is used (memory-level parallelism).
-    float v[KP];
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
-      v[k] = 0.f;
-      if (in && k < a.nlev) {
-        const int slot = (a.level0 + k) % a.nslots;
-        v[k] = __ldcs(ring + (long long)slot * a.slot_stride + pt);
-      }
+      const int sl = slot0 + k >= a.nslots ? slot0 + k - a.nslots : slot0 + k;
+      av[k] = (in && k < a.nlev) ? __ldcs(ring + (long long)sl * a.slot_stride + pt) : 0.f;
     }
+#pragma unroll
+    for (int i = 0; i < PC; ++i) pv[i] = (in && i < a.r) ? __ldcs(P + (long long)i * a.M + pt) : 0.f;
+  };
+  if ((long long)blockIdx.x < ntiles) load_tile(blockIdx.x);
+
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long m0 = tile * TILE_M;
+    // 1. split the snapshots into tf32 hi + lo and stage them K-major
 #pragma unroll
     for (int k4 = 0; k4 < KP; k4 += 4) {
       float4 hi, lo;
-      hi.x = tf32_hi(v[k4 + 0]); hi.y = tf32_hi(v[k4 + 1]); hi.z = tf32_hi(v[k4 + 2]); hi.w = tf32_hi(v[k4 + 3]);
-      lo.x = v[k4 + 0] - hi.x; lo.y = v[k4 + 1] - hi.y; lo.z = v[k4 + 2] - hi.z; lo.w = v[k4 + 3] - hi.w;
+      hi.x = tf32_hi(av[k4 + 0]); hi.y = tf32_hi(av[k4 + 1]); hi.z = tf32_hi(av[k4 + 2]); hi.w = tf32_hi(av[k4 + 3]);
+      lo.x = av[k4 + 0] - hi.x; lo.y = av[k4 + 1] - hi.y; lo.z = av[k4 + 2] - hi.z; lo.w = av[k4 + 3] - hi.w;
       const uint32_t o = kmaj_off(tid, k4, KP);
       *reinterpret_cast<float4*>(A_hi + o) = hi;
       *reinterpret_cast<float4*>(A_lo + o) = lo;
@@ -195,7 +205,12 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
                    : "memory");
     }
     __syncwarp();
-    // 3. epilogue: TMEM lanes 32*warp.. -> P (coalesced per probe column)
+    // 3. while the tensor cores run, fetch the next tile
+    float pc[PC > 0 ? PC : 1];
+#pragma unroll
+    for (int i = 0; i < PC; ++i) pc[i] = pv[i];
+    if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x);
+    // 4. epilogue: TMEM lanes 32*warp.. -> P (coalesced per probe column)
     const int all_done = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
     if (!all_done) {
       ok = false;
@@ -204,18 +219,33 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-      const long long prow = m0 + warp * 32 + lane;
-      for (int c0 = 0; c0 < NP; c0 += 16) {
-        float acc[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
-        if (prow < a.M) {
-          float old[16];
+      const long long prow = m0 + warp * 32 + (tid & 31);
+      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      if (PC > 0) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            old[j] = (c0 + j < a.r) ? P[(long long)(c0 + j) * a.M + prow] : 0.f;
+        for (int c = 0; c < (PC > 0 ? PC / 16 : 1); ++c) {
+          if (c * 16 < NP) {  // uniform
+            float acc[16];
+            tmem_ld16(trow + (uint32_t)(c * 16), acc);
+            if (prow < a.M) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + j < a.r) P[(long long)(c0 + j) * a.M + prow] = old[j] + acc[j];
+              for (int j = 0; j < 16; ++j)
+                if (c * 16 + j < a.r) P[(long long)(c * 16 + j) * a.M + prow] = pc[c * 16 + j] + acc[j];
+            }
+          }
+        }
+      } else {
+        for (int c0 = 0; c0 < NP; c0 += 16) {
+          float acc[16];
+          tmem_ld16(trow + (uint32_t)c0, acc);
+          if (prow < a.M) {
+            float old[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) old[j] = (c0 + j < a.r) ? P[(long long)(c0 + j) * a.M + prow] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < a.r) P[(long long)(c0 + j) * a.M + prow] = old[j] + acc[j];
+          }
         }
       }
     }
@@ -229,27 +259,30 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
   }
 }
 
-template <int KP>
+template <int KP, int PC>
 cudaError_t launch_kp(const GemmArgs& a, cudaStream_t s) {
   const int NP = std::max(16, (a.r + 15) / 16 * 16);
   int ncols = 32;
   while (ncols < NP) ncols <<= 1;
   const size_t smem = (size_t)2 * TILE_M * KP * 4 + (size_t)2 * NP * KP * 4 + 16;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(probe_gemm_tf32<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr_set = true;
+  static int regs = 0;
+  if (regs == 0) {
+    cudaFuncSetAttribute(probe_gemm_tf32<KP, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncAttributes fa;
+    regs = cudaFuncGetAttributes(&fa, probe_gemm_tf32<KP, PC>) == cudaSuccess ? std::max(fa.numRegs, 1) : 255;
   }
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, probe_gemm_tf32<KP>, TILE_M, smem);
-  occ = std::max(1, std::min(occ, 512 / ncols));
+  // CTAs per SM: registers, shared memory (228 KB, 1 KB reserved per CTA), TMEM columns
+  const int by_regs = 65536 / (((regs + 7) / 8 * 8) * TILE_M);
+  const int by_smem = (int)((228 * 1024) / (smem + 1024));
+  const int by_tmem = 512 / ncols;
+  const int occ = std::max(1, std::min(std::min(by_regs, by_smem), std::min(by_tmem, 8)));
   const long long ntiles = (a.M + TILE_M - 1) / TILE_M;
   const long long grid_x = std::min<long long>(ntiles, (long long)sms * occ);
   dim3 grid((unsigned)grid_x, a.nshots);
-  probe_gemm_tf32<KP><<<grid, TILE_M, smem, s>>>(a, NP, ncols, ntiles);
+  probe_gemm_tf32<KP, PC><<<grid, TILE_M, smem, s>>>(a, NP, ncols, ntiles);
   return cudaGetLastError();
 }
 
@@ -260,7 +293,9 @@ int gemm_kpad(int T) { return T <= 32 ? 32 : 64; }
 cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
   if (a.nlev <= 0) return cudaSuccess;
   prof_before(2, s);  // TP_KERNEL_PROBE_GEMM
-  cudaError_t e = a.nlev <= 32 ? launch_kp<32>(a, s) : launch_kp<64>(a, s);
+  cudaError_t e;
+  if (a.nlev <= 32) e = a.r <= 16 ? launch_kp<32, 16>(a, s) : (a.r <= 32 ? launch_kp<32, 32>(a, s) : launch_kp<32, 0>(a, s));
+  else e = a.r <= 16 ? launch_kp<64, 16>(a, s) : (a.r <= 32 ? launch_kp<64, 32>(a, s) : launch_kp<64, 0>(a, s));
   prof_after(2, s);
   return e;
 }

@@ -45,19 +45,31 @@ Weights stencil_weights(int order);
 // ---------------------------------------------------------------- stencil
 enum StencilMode { MODE_STEP = 0, MODE_IMAGE = 1 };
 
+// A field of a "family": `nfields` consecutive padded fields starting at
+// `base` (a ring of levels, a history, the accumulators...).  Shot s uses
+// field f0 + s * fs (fs = 0: one field shared by all shots).
+struct FieldRef {
+  const float* base;
+  int nfields;
+  int f0;
+  int fs;
+  __host__ __device__ const float* ptr(const Layout& L, int shot) const {
+    return base + (long long)(f0 + shot * fs) * L.field;
+  }
+};
+
 // MODE_STEP : out = 2 src - p1 + p2 * S(src)          (leapfrog, p1 = older level, p2 = c2)
 // MODE_IMAGE: out = p2 + p1 * S(src)  (out may alias p2: accumulate)
-// S(.) = sum of stencil weights (no 1/h^2).  Pointers are shot-0 bases;
-// *_ss are per-shot strides in floats (0 = shared by all shots).
+// S(.) = sum of stencil weights (no 1/h^2).  `out` is the shot-0 field,
+// out_ss the per-shot stride in floats.
 struct StencilArgs {
-  const float* src;  long long src_ss;
-  const float* p1;   long long p1_ss;
-  const float* p2;   long long p2_ss;
-  float* out;        long long out_ss;
+  FieldRef src, p1, p2;
+  float* out;
+  long long out_ss;
   int nshots;
 };
 cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& a,
-                           cudaStream_t s);
+                           cudaStream_t s, int* err);
 
 // ---------------------------------------------------------------- probe GEMM
 // P[s][i][x] += sum_{k < nlev} ring[s][(level0 + k) mod nslots][x] * Q[s][level0 + k + qshift][i]

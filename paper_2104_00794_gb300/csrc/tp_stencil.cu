@@ -12,12 +12,23 @@
 //   * zero halo layers of the padded layout supply the Dirichlet boundary,
 //     so no load is predicated.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "tp_internal.h"
 
 namespace tp {
 
 namespace {
+
+// pointer + per-shot stride form used by the plain sweeps
+struct PlainArgs {
+  const float* src;  long long src_ss;
+  const float* p1;   long long p1_ss;
+  const float* p2;   long long p2_ss;
+  float* out;        long long out_ss;
+  int nshots;
+};
 
 __device__ __forceinline__ float4 ld4(const float* base, long long idx) {
   return __ldg(reinterpret_cast<const float4*>(base + idx));
@@ -50,7 +61,7 @@ constexpr int T3Y = 16;  // rows per tile
 
 template <int R, int MODE>
 __global__ void __launch_bounds__(T3X * T3Y, 2)
-sweep3d(Layout L, Weights W, StencilArgs a, int bz, int nzc) {
+sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
   __shared__ float4 sm[T3Y + 2 * R][T3X + 2];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int shot = blockIdx.z / nzc, zc = blockIdx.z % nzc;
@@ -143,7 +154,7 @@ constexpr int W2 = 4;  // warps per CTA, each an independent (x strip, z chunk)
 
 template <int R, int MODE>
 __global__ void __launch_bounds__(32 * W2)
-sweep2d(Layout L, Weights W, StencilArgs a, int bz, int nzc, int nxt, int nwarps) {
+sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) {
   __shared__ float4 sm[W2][32 + 2];
   const int lane = threadIdx.x, wi = threadIdx.y;
   const int gw = blockIdx.x * W2 + wi;
@@ -225,7 +236,7 @@ int num_sms() {
 }
 
 template <int R, int MODE>
-cudaError_t launch3d(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s) {
+cudaError_t launch3d(const Layout& L, const Weights& W, const PlainArgs& a, cudaStream_t s) {
   static int occ = 0;
   if (occ == 0) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep3d<R, MODE>, T3X * T3Y, 0);
@@ -244,7 +255,7 @@ cudaError_t launch3d(const Layout& L, const Weights& W, const StencilArgs& a, cu
 }
 
 template <int R, int MODE>
-cudaError_t launch2d(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s) {
+cudaError_t launch2d(const Layout& L, const Weights& W, const PlainArgs& a, cudaStream_t s) {
   const int nxt = (L.nx + 127) / 128;
   const long long strips = (long long)nxt * a.nshots;
   const long long target = 16LL * W2 * num_sms();  // warps
@@ -260,17 +271,32 @@ cudaError_t launch2d(const Layout& L, const Weights& W, const StencilArgs& a, cu
 
 }  // namespace
 
-cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& a,
-                           cudaStream_t s) {
+cudaError_t launch_sweep3d_tma(int mode, const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s,
+                               int* err);
+
+// 3-D sweeps use the TMA-pipelined kernel (tp_sweep3d_tma.cu); the register
+// queue kernel above stays selectable with TP_SWEEP3D=plain for comparisons.
+cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& sa,
+                           cudaStream_t s, int* err) {
   const int kind = mode == MODE_STEP ? 0 : 1;  // TP_KERNEL_STENCIL / TP_KERNEL_IMAGING
+  static const bool plain3d = [] {
+    const char* e = getenv("TP_SWEEP3D");
+    return e && strcmp(e, "plain") == 0;
+  }();
   prof_before(kind, s);
   cudaError_t e;
-  if (L.ndim == 3) {
-    if (W.R == 4) e = mode == MODE_STEP ? launch3d<4, MODE_STEP>(L, W, a, s) : launch3d<4, MODE_IMAGE>(L, W, a, s);
-    else e = mode == MODE_STEP ? launch3d<2, MODE_STEP>(L, W, a, s) : launch3d<2, MODE_IMAGE>(L, W, a, s);
+  if (L.ndim == 3 && !plain3d) {
+    e = launch_sweep3d_tma(mode, L, W, sa, s, err);
   } else {
-    if (W.R == 4) e = mode == MODE_STEP ? launch2d<4, MODE_STEP>(L, W, a, s) : launch2d<4, MODE_IMAGE>(L, W, a, s);
-    else e = mode == MODE_STEP ? launch2d<2, MODE_STEP>(L, W, a, s) : launch2d<2, MODE_IMAGE>(L, W, a, s);
+    PlainArgs a{sa.src.ptr(L, 0), (long long)sa.src.fs * L.field, sa.p1.ptr(L, 0), (long long)sa.p1.fs * L.field,
+                sa.p2.ptr(L, 0), (long long)sa.p2.fs * L.field, sa.out, sa.out_ss, sa.nshots};
+    if (L.ndim == 3) {
+      if (W.R == 4) e = mode == MODE_STEP ? launch3d<4, MODE_STEP>(L, W, a, s) : launch3d<4, MODE_IMAGE>(L, W, a, s);
+      else e = mode == MODE_STEP ? launch3d<2, MODE_STEP>(L, W, a, s) : launch3d<2, MODE_IMAGE>(L, W, a, s);
+    } else {
+      if (W.R == 4) e = mode == MODE_STEP ? launch2d<4, MODE_STEP>(L, W, a, s) : launch2d<4, MODE_IMAGE>(L, W, a, s);
+      else e = mode == MODE_STEP ? launch2d<2, MODE_STEP>(L, W, a, s) : launch2d<2, MODE_IMAGE>(L, W, a, s);
+    }
   }
   prof_after(kind, s);
   return e;

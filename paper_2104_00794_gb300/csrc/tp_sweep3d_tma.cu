@@ -1,0 +1,395 @@
+// 3-D leapfrog / imaging sweep with TMA-staged planes (sm_103a).
+//
+// Algorithm 1 lines 1 and 5 (operators f and f^T) are one 2k-order star
+// stencil per time step: out = 2u - u_old + c2 * S(u), S = 3 w0 u + sum_k w_k
+// (six neighbours at distance k).  The kernel is HBM-bound (16 B per point:
+// read u, u_old, c2; write out).  Design:
+//   * work = (x-y tile of 64 x 16 points, z plane) pairs of all shots, split
+//     evenly over a persistent grid (2 CTAs per SM); each CTA sweeps its
+//     contiguous run of planes in z (a run may span several tiles);
+//   * one producer thread streams, with cp.async.bulk.tensor (4-D tensor
+//     maps over the padded field families), the haloed u plane
+//     [16+2R][64+8] and the u_old / c2 planes [16][64] into a ring of shared
+//     memory stages guarded by mbarriers (full: TMA transaction bytes,
+//     empty: one arrival per consumer warp), R+1+3 u planes deep so three
+//     planes are in flight while R+1 are resident;
+//   * 256 consumer threads own 4 consecutive x points each; the z neighbours
+//     live in a register queue of 2R+1 float4, x/y neighbours are read from
+//     the resident centre plane (x halo from the box, zero halo layers from
+//     the padded layout), so every value crosses HBM about once per step;
+//   * every wait is bounded (clock64); on a timeout the CTA sets bit 0 of
+//     *err, stops issuing, drains its own copies (bounded) and exits.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "tp_internal.h"
+
+namespace tp {
+
+namespace {
+
+constexpr int BX = 64, BY = 16, LA = 3;
+constexpr int NCONS = 256;                 // consumer threads (16 x 16)
+constexpr int NTHREADS = NCONS + 32;       // + one producer warp
+constexpr long long SPIN_LIMIT = 2000000000LL;  // cycles (~1 s)
+
+template <int R>
+struct Cfg {
+  static constexpr int NSU = R + 1 + LA;  // u stages
+  static constexpr int NSP = LA + 1;      // u_old / c2 stages
+  static constexpr int UW = BX + 8, UH = BY + 2 * R;
+  static constexpr int UFL = UW * UH, PFL = BX * BY;
+  static constexpr uint32_t UBYTES = UFL * 4, PBYTES = PFL * 4;
+  static constexpr size_t BAR_OFF = (size_t)(NSU * UFL + 2 * NSP * PFL) * 4;
+  static constexpr size_t SMEM = BAR_OFF + (size_t)(2 * NSU + 2 * NSP) * 8 + 16;
+};
+
+struct TmaArgs {
+  Layout L;
+  Weights W;
+  int f_src, fs_src, f_p1, fs_p1, f_p2, fs_p2;
+  float* out;
+  long long out_ss;
+  int nshots, ntx, nty;
+  long long work;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint32_t b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n));
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint32_t b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(b), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on timeout or when another role has aborted
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, volatile int* abort_flag) {
+  if (bar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!bar_try(b, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > SPIN_LIMIT) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma4(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                     uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ float comp(const float4& v, int p) {
+  return p == 0 ? v.x : (p == 1 ? v.y : (p == 2 ? v.z : v.w));
+}
+
+struct Seg {
+  int shot, x0, y0, z0, z1;
+};
+
+__device__ __forceinline__ Seg segment(const TmaArgs& a, long long idx, long long end) {
+  const int nz = a.L.nz;
+  const long long item = idx / nz;
+  Seg s;
+  s.z0 = (int)(idx % nz);
+  s.z1 = (int)std::min<long long>(nz, s.z0 + (end - idx));
+  const int per = a.ntx * a.nty;
+  s.shot = (int)(item / per);
+  const int t = (int)(item % per);
+  s.x0 = (t % a.ntx) * BX;
+  s.y0 = (t / a.ntx) * BY;
+  return s;
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(NTHREADS, 2)
+sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mP1,
+            const __grid_constant__ CUtensorMap mP2, TmaArgs a) {
+  using C = Cfg<R>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* sU = reinterpret_cast<float*>(smem);
+  float* sP1 = sU + C::NSU * C::UFL;
+  float* sP2 = sP1 + C::NSP * C::PFL;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
+  const uint32_t fullU = su32(bars), emptyU = fullU + 8 * C::NSU;
+  const uint32_t fullP = emptyU + 8 * C::NSU, emptyP = fullP + 8 * C::NSP;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * C::NSU + 2 * C::NSP);
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < C::NSU; ++s) {
+      bar_init(fullU + 8 * s, 1);
+      bar_init(emptyU + 8 * s, NCONS / 32);
+    }
+    for (int s = 0; s < C::NSP; ++s) {
+      bar_init(fullP + 8 * s, 1);
+      bar_init(emptyP + 8 * s, NCONS / 32);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const long long per = a.work / gridDim.x, rem = a.work % gridDim.x;
+  const long long start = blockIdx.x * per + std::min<long long>(blockIdx.x, rem);
+  const long long end = start + per + (blockIdx.x < rem ? 1 : 0);
+
+  if (tid >= NCONS) {
+    // ------------------------------------------------------------ producer
+    if (tid != NCONS) return;
+    uint32_t ku = 0, kp = 0;
+    bool ok = true;
+    for (long long idx = start; idx < end && ok;) {
+      const Seg sg = segment(a, idx, end);
+      const int nzs = sg.z1 - sg.z0;
+      const int fu = a.f_src + sg.shot * a.fs_src, f1 = a.f_p1 + sg.shot * a.fs_p1, f2 = a.f_p2 + sg.shot * a.fs_p2;
+      for (int k = 0; k < nzs + 2 * R && ok; ++k) {
+        const int su = ku % C::NSU;
+        if (ku >= (uint32_t)C::NSU && !bar_wait(emptyU + 8 * su, ((ku / C::NSU) - 1) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        bar_expect_tx(fullU + 8 * su, C::UBYTES);
+        // haloed u plane z = z0 - R + k: padded x from x0 (= x0 - 4 + H), y from y0 - R + H
+        tma4(su32(sU + su * C::UFL), &mU, sg.x0, sg.y0 - R + H, sg.z0 - R + k + H, fu, fullU + 8 * su);
+        ++ku;
+        if (k >= 2 * R) {
+          const int j = k - 2 * R;
+          const int sp = kp % C::NSP;
+          if (kp >= (uint32_t)C::NSP && !bar_wait(emptyP + 8 * sp, ((kp / C::NSP) - 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          bar_expect_tx(fullP + 8 * sp, 2 * C::PBYTES);
+          tma4(su32(sP1 + sp * C::PFL), &mP1, sg.x0 + H, sg.y0 + H, sg.z0 + j + H, f1, fullP + 8 * sp);
+          tma4(su32(sP2 + sp * C::PFL), &mP2, sg.x0 + H, sg.y0 + H, sg.z0 + j + H, f2, fullP + 8 * sp);
+          ++kp;
+        }
+      }
+      idx += nzs;
+    }
+    if (!ok) atomicOr(a.err, 1);
+    // drain: wait (bounded) until every copy this thread issued has landed
+    for (int s = 0; s < C::NSU; ++s) {
+      const uint32_t uses = ku > (uint32_t)s ? (ku - 1 - s) / C::NSU + 1 : 0;
+      if (uses) {
+        const long long t0 = clock64();
+        while (!bar_try(fullU + 8 * s, (uses - 1) & 1) && clock64() - t0 < SPIN_LIMIT) {}
+      }
+    }
+    for (int s = 0; s < C::NSP; ++s) {
+      const uint32_t uses = kp > (uint32_t)s ? (kp - 1 - s) / C::NSP + 1 : 0;
+      if (uses) {
+        const long long t0 = clock64();
+        while (!bar_try(fullP + 8 * s, (uses - 1) & 1) && clock64() - t0 < SPIN_LIMIT) {}
+      }
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  const int tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+  constexpr int RW = C::UW / 4;  // float4 per staged row
+  const float4* U4 = reinterpret_cast<const float4*>(sU);
+  const float w0 = 3.0f * a.W.w[0];
+  uint32_t ku = 0, kp = 0;
+  bool ok = true;
+  for (long long idx = start; idx < end && ok;) {
+    const Seg sg = segment(a, idx, end);
+    const int nzs = sg.z1 - sg.z0;
+    const int x = sg.x0 + 4 * tx, y = sg.y0 + ty;
+    float* out = a.out + sg.shot * a.out_ss;
+    const int cidx = (ty + R) * RW + tx + 1;  // own float4 in a staged u plane
+    float4 q[2 * R + 1];
+    // prologue: planes z0-R .. z0+R-1 fill the queue; the first R are released
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) {
+      const uint32_t kk = ku + k, s = kk % C::NSU;
+      if (!bar_wait(fullU + 8 * s, (kk / C::NSU) & 1, abort_flag)) { ok = false; break; }
+      q[k] = U4[s * (C::UFL / 4) + cidx];
+      if (k < R) {
+        __syncwarp();
+        if (lane == 0) bar_arrive(emptyU + 8 * s);
+      }
+    }
+    for (int j = 0; j < nzs && ok; ++j) {
+      const uint32_t kc = ku + j + R, kn = ku + j + 2 * R, kq = kp + j;
+      const uint32_t sc = kc % C::NSU, sn = kn % C::NSU, sp = kq % C::NSP;
+      if (!bar_wait(fullU + 8 * sn, (kn / C::NSU) & 1, abort_flag)) { ok = false; break; }
+      q[2 * R] = U4[sn * (C::UFL / 4) + cidx];
+      if (!bar_wait(fullP + 8 * sp, (kq / C::NSP) & 1, abort_flag)) { ok = false; break; }
+      const float4* Uc = U4 + sc * (C::UFL / 4);
+      const float4 xl = Uc[cidx - 1], xc = Uc[cidx], xr = Uc[cidx + 1];
+      const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
+      float s4[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) s4[p] = w0 * v[4 + p];
+#pragma unroll
+      for (int k = 1; k <= R; ++k) {
+        const float4 yp = Uc[cidx + k * RW], ym = Uc[cidx - k * RW];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const float t = (v[4 + p + k] + v[4 + p - k]) + (comp(yp, p) + comp(ym, p)) +
+                          (comp(q[R + k], p) + comp(q[R - k], p));
+          s4[p] = fmaf(a.W.w[k], t, s4[p]);
+        }
+      }
+      const float4 c1 = reinterpret_cast<const float4*>(sP1 + sp * C::PFL)[ty * (BX / 4) + tx];
+      const float4 c2 = reinterpret_cast<const float4*>(sP2 + sp * C::PFL)[ty * (BX / 4) + tx];
+      float res[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const float c = v[4 + p];
+        res[p] = MODE == MODE_STEP ? fmaf(comp(c2, p), s4[p], 2.0f * c - comp(c1, p))
+                                   : fmaf(comp(c1, p), s4[p], comp(c2, p));
+      }
+      __syncwarp();
+      if (lane == 0) {
+        bar_arrive(emptyU + 8 * sc);
+        bar_arrive(emptyP + 8 * sp);
+      }
+      if (y < a.L.ny && x < a.L.nx) {
+        const long long o = a.L.off(sg.z0 + j, y, x);
+        if (x + 3 < a.L.nx) {
+          *reinterpret_cast<float4*>(out + o) = make_float4(res[0], res[1], res[2], res[3]);
+        } else {
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+            if (x + p < a.L.nx) out[o + p] = res[p];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
+    }
+    if (!ok) break;
+    // the last R planes were only queue heads: release them
+    for (int k = nzs + R; k < nzs + 2 * R; ++k) {
+      __syncwarp();
+      if (lane == 0) bar_arrive(emptyU + 8 * ((ku + k) % C::NSU));
+    }
+    ku += nzs + 2 * R;
+    kp += nzs;
+    idx += nzs;
+  }
+  if (!ok && lane == 0) atomicOr(a.err, 1);
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+struct MapKey {
+  const void* base;
+  int nfields, bw, bh;
+  long long field;
+  int px, py, pz;
+  bool operator==(const MapKey& o) const {
+    return base == o.base && nfields == o.nfields && bw == o.bw && bh == o.bh && field == o.field && px == o.px &&
+           py == o.py && pz == o.pz;
+  }
+};
+
+// Small cache of encoded maps (the buffers of one call are few and stable).
+bool get_map(const Layout& L, const FieldRef& f, int bw, int bh, CUtensorMap* out) {
+  static std::mutex m;
+  static std::vector<std::pair<MapKey, CUtensorMap>> cache;
+  const MapKey key{f.base, f.nfields, bw, bh, L.field, L.px, L.py, L.pz};
+  std::lock_guard<std::mutex> lk(m);
+  for (auto& e : cache)
+    if (e.first == key) {
+      *out = e.second;
+      return true;
+    }
+  EncodeFn enc = encode_fn();
+  if (!enc) return false;
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)L.px, (cuuint64_t)L.py, (cuuint64_t)L.pz, (cuuint64_t)f.nfields};
+  const cuuint64_t strides[3] = {(cuuint64_t)L.px * 4, (cuuint64_t)L.plane * 4, (cuuint64_t)L.field * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)bw, (cuuint32_t)bh, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(f.base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  if (cache.size() >= 64) cache.erase(cache.begin());
+  cache.emplace_back(key, map);
+  *out = map;
+  return true;
+}
+
+template <int R, int MODE>
+cudaError_t launch_t(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
+  using C = Cfg<R>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(sweep3d_tma<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    attr = true;
+  }
+  CUtensorMap mU, m1, m2;
+  if (!get_map(L, a.src, C::UW, C::UH, &mU) || !get_map(L, a.p1, BX, BY, &m1) || !get_map(L, a.p2, BX, BY, &m2))
+    return cudaErrorInvalidValue;
+  TmaArgs t;
+  t.L = L;
+  t.W = W;
+  t.f_src = a.src.f0; t.fs_src = a.src.fs;
+  t.f_p1 = a.p1.f0; t.fs_p1 = a.p1.fs;
+  t.f_p2 = a.p2.f0; t.fs_p2 = a.p2.fs;
+  t.out = a.out;
+  t.out_ss = a.out_ss;
+  t.nshots = a.nshots;
+  t.ntx = (L.nx + BX - 1) / BX;
+  t.nty = (L.ny + BY - 1) / BY;
+  t.work = (long long)t.ntx * t.nty * a.nshots * L.nz;
+  t.err = err;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long blocks = std::min<long long>(t.work, 2LL * sms);
+  sweep3d_tma<R, MODE><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, t);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sweep3d_tma(int mode, const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s,
+                               int* err) {
+  if (W.R == 4) return mode == MODE_STEP ? launch_t<4, MODE_STEP>(L, W, a, s, err) : launch_t<4, MODE_IMAGE>(L, W, a, s, err);
+  return mode == MODE_STEP ? launch_t<2, MODE_STEP>(L, W, a, s, err) : launch_t<2, MODE_IMAGE>(L, W, a, s, err);
+}
+
+}  // namespace tp
