@@ -83,7 +83,7 @@ Layout make_layout(int ndim, int nx, int ny, int nz) {
   L.nx = nx;
   L.ny = ny;
   L.nz = nz;
-  L.px = (int)round_up(nx, XALIGN) + 2 * H;
+  L.px = (int)round_up(HX + round_up(nx, XALIGN) + 8, 16);
   L.py = ndim == 3 ? (int)round_up(ny, YALIGN) + 2 * H : 1;
   L.pz = nz + 2 * H;
   L.plane = (long long)L.py * L.px;

@@ -211,7 +211,8 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
     for (int i = 0; i < PC; ++i) pc[i] = pv[i];
     if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x);
     // 4. epilogue: TMEM lanes 32*warp.. -> P (coalesced per probe column)
-    const int all_done = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
+    // one thread polls the barrier; the others wait at the CTA barrier
+    const int all_done = __syncthreads_and(tid == 0 ? (mbar_wait(bar, phase) ? 1 : 0) : 1);
     if (!all_done) {
       ok = false;
       if (tid == 0) atomicExch(a.err, 1);

@@ -7,16 +7,19 @@
 
 namespace tp {
 
-// Halo width of every padded field: zero layers around the grid that make
-// the Dirichlet boundary of the Laplacian free (covers radius R <= 4).
+// Halo width of every padded field in y and z: zero layers around the grid
+// that make the Dirichlet boundary of the Laplacian free (radius R <= 4).
 constexpr int H = 4;
+// x halo: 8 zero columns, so that every row's interior starts on a 32-byte
+// DRAM sector (rows are 64-byte multiples); x0 - 4 boxes stay 16-byte aligned.
+constexpr int HX = 8;
 // x extents are padded to a multiple of this (tile widths of the sweeps).
 constexpr int XALIGN = 128;
 // y extents (3-D) are padded to a multiple of this.
 constexpr int YALIGN = 16;
 
 // Geometry of a padded field.  Grid node (z, y, x) lives at
-//   (z + H) * plane + (y + yh) * px + (x + H),  yh = H in 3-D, 0 in 2-D.
+//   (z + H) * plane + (y + yh) * px + (x + HX),  yh = H in 3-D, 0 in 2-D.
 // Padding and halo cells are zero and never written by the kernels.
 struct Layout {
   int ndim, nx, ny, nz;
@@ -24,7 +27,7 @@ struct Layout {
   long long plane;      // py * px
   long long field;      // pz * plane, rounded up to 64 floats (256 B)
   __host__ __device__ long long off(long long z, long long y, long long x) const {
-    return (z + H) * plane + (y + (ndim == 3 ? H : 0)) * px + (x + H);
+    return (z + H) * plane + (y + (ndim == 3 ? H : 0)) * px + (x + HX);
   }
   __host__ __device__ long long off_flat(long long idx) const {  // dense (z*ny+y)*nx+x
     long long x = idx % nx, t = idx / nx;

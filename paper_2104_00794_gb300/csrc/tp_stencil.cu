@@ -76,11 +76,11 @@ sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
   float* out = a.out + shot * a.out_ss;
   const long long pl = L.plane;
   // offset of (z = 0, row, column) for this thread's own points and halos
-  const long long colc = (long long)(y + H) * L.px + (x + H) + (long long)H * pl;
-  const long long coly0 = (long long)(y0 - R + ty + H) * L.px + (x + H) + (long long)H * pl;
-  const long long coly1 = (long long)(y0 + T3Y + ty + H) * L.px + (x + H) + (long long)H * pl;
-  const long long colxl = (long long)(y + H) * L.px + (x0 - 4 + H) + (long long)H * pl;
-  const long long colxr = (long long)(y + H) * L.px + (x0 + 4 * T3X + H) + (long long)H * pl;
+  const long long colc = (long long)(y + H) * L.px + (x + HX) + (long long)H * pl;
+  const long long coly0 = (long long)(y0 - R + ty + H) * L.px + (x + HX) + (long long)H * pl;
+  const long long coly1 = (long long)(y0 + T3Y + ty + H) * L.px + (x + HX) + (long long)H * pl;
+  const long long colxl = (long long)(y + H) * L.px + (x0 - 4 + HX) + (long long)H * pl;
+  const long long colxr = (long long)(y + H) * L.px + (x0 + 4 * T3X + HX) + (long long)H * pl;
   const bool hy = ty < R, hxl = tx == 0, hxr = tx == T3X - 1;
 
   float4 q[2 * R + 1];
@@ -171,9 +171,9 @@ sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) 
   const float* p2 = a.p2 + shot * a.p2_ss;
   float* out = a.out + shot * a.out_ss;
   const long long pl = L.px;  // row pitch (plane == px in 2-D)
-  const long long colc = (long long)(x + H) + (long long)H * pl;
-  const long long colxl = (long long)(x0 - 4 + H) + (long long)H * pl;
-  const long long colxr = (long long)(x0 + 128 + H) + (long long)H * pl;
+  const long long colc = (long long)(x + HX) + (long long)H * pl;
+  const long long colxl = (long long)(x0 - 4 + HX) + (long long)H * pl;
+  const long long colxr = (long long)(x0 + 128 + HX) + (long long)H * pl;
   const bool hxl = lane == 0, hxr = lane == 31;
 
   float4 q[2 * R + 1];

@@ -171,8 +171,8 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
           break;
         }
         bar_expect_tx(fullU + 8 * su, C::UBYTES);
-        // haloed u plane z = z0 - R + k: padded x from x0 (= x0 - 4 + H), y from y0 - R + H
-        tma4(su32(sU + su * C::UFL), &mU, sg.x0, sg.y0 - R + H, sg.z0 - R + k + H, fu, fullU + 8 * su);
+        // haloed u plane z = z0 - R + k: padded x from x0 - 4 + HX, y from y0 - R + H
+        tma4(su32(sU + su * C::UFL), &mU, sg.x0 - 4 + HX, sg.y0 - R + H, sg.z0 - R + k + H, fu, fullU + 8 * su);
         ++ku;
         if (k >= 2 * R) {
           const int j = k - 2 * R;
@@ -182,8 +182,8 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
             break;
           }
           bar_expect_tx(fullP + 8 * sp, 2 * C::PBYTES);
-          tma4(su32(sP1 + sp * C::PFL), &mP1, sg.x0 + H, sg.y0 + H, sg.z0 + j + H, f1, fullP + 8 * sp);
-          tma4(su32(sP2 + sp * C::PFL), &mP2, sg.x0 + H, sg.y0 + H, sg.z0 + j + H, f2, fullP + 8 * sp);
+          tma4(su32(sP1 + sp * C::PFL), &mP1, sg.x0 + HX, sg.y0 + H, sg.z0 + j + H, f1, fullP + 8 * sp);
+          tma4(su32(sP2 + sp * C::PFL), &mP2, sg.x0 + HX, sg.y0 + H, sg.z0 + j + H, f2, fullP + 8 * sp);
           ++kp;
         }
       }
