@@ -83,11 +83,12 @@ Layout make_layout(int ndim, int nx, int ny, int nz) {
   L.nx = nx;
   L.ny = ny;
   L.nz = nz;
-  L.px = (int)round_up(HX + round_up(nx, XALIGN) + 8, 16);
+  // the right x halo of a row is the left padding of the next row (zeros)
+  L.px = (int)(HX + round_up(nx, XALIGN));
   L.py = ndim == 3 ? (int)round_up(ny, YALIGN) + 2 * H : 1;
   L.pz = nz + 2 * H;
   L.plane = (long long)L.py * L.px;
-  L.field = round_up((long long)L.pz * L.plane, 64);
+  L.field = round_up((long long)L.pz * L.plane + 64, 64);  // + slack: the last row's right halo
   return L;
 }
 
@@ -446,7 +447,7 @@ tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_
   GemmArgs g{};
   g.ring = c.at<float>(P.o_f); g.slot_stride = P.L.field; g.ring_ss = ring_ss; g.nslots = S;
   g.Q = Q; g.nt = nt; g.r = r; g.q_ss = (long long)nt * r;
-  g.M = P.L.field; g.nshots = P.nshots; g.qlo = 2; g.qhi = nt - 1;
+  g.L = P.L; g.pstride = P.L.field; g.nshots = P.nshots; g.qlo = 2; g.qhi = nt - 1;
   g.q_has_lo = (P.kind == TP_PROBE_GAUSSIAN || P.kind == TP_PROBE_USER) ? 1 : 0;
   g.err = c.err();
 

@@ -161,21 +161,28 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
   // register prefetch of one tile: the snapshots (A) and the old accumulators
   float av[KP];
   float pv[PC > 0 ? PC : 1];
+  // tile -> (grid row, 128-point segment) -> padded offset of its first point
+  const int nxt = (a.L.nx + TILE_M - 1) / TILE_M;
+  auto tile_base = [&](long long tile) -> long long {
+    const long long row = tile / nxt;
+    const int xb = (int)(tile % nxt);
+    return a.L.off(row / a.L.ny, row % a.L.ny, (long long)xb * TILE_M);
+  };
   auto load_tile = [&](long long tile) {
-    const long long pt = tile * TILE_M + tid;
-    const bool in = pt < a.M;
+    const long long pt = tile_base(tile) + tid;
+    const bool in = true;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
       const int sl = slot0 + k >= a.nslots ? slot0 + k - a.nslots : slot0 + k;
       av[k] = (in && k < a.nlev) ? __ldcs(ring + (long long)sl * a.slot_stride + pt) : 0.f;
     }
 #pragma unroll
-    for (int i = 0; i < PC; ++i) pv[i] = (in && i < a.r) ? __ldcs(P + (long long)i * a.M + pt) : 0.f;
+    for (int i = 0; i < PC; ++i) pv[i] = (in && i < a.r) ? __ldcs(P + (long long)i * a.pstride + pt) : 0.f;
   };
   if ((long long)blockIdx.x < ntiles) load_tile(blockIdx.x);
 
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const long long m0 = tile * TILE_M;
+    const long long m0 = tile_base(tile);
     // 1. split the snapshots into tf32 hi + lo and stage them K-major
 #pragma unroll
     for (int k4 = 0; k4 < KP; k4 += 4) {
@@ -220,7 +227,7 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-      const long long prow = m0 + warp * 32 + (tid & 31);
+      const long long prow = m0 + warp * 32 + (tid & 31);  // padded offset of this lane's point
       const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
       if (PC > 0) {
 #pragma unroll
@@ -228,10 +235,10 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
           if (c * 16 < NP) {  // uniform
             float acc[16];
             tmem_ld16(trow + (uint32_t)(c * 16), acc);
-            if (prow < a.M) {
+            {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
-                if (c * 16 + j < a.r) P[(long long)(c * 16 + j) * a.M + prow] = pc[c * 16 + j] + acc[j];
+                if (c * 16 + j < a.r) P[(long long)(c * 16 + j) * a.pstride + prow] = pc[c * 16 + j] + acc[j];
             }
           }
         }
@@ -239,13 +246,13 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
         for (int c0 = 0; c0 < NP; c0 += 16) {
           float acc[16];
           tmem_ld16(trow + (uint32_t)c0, acc);
-          if (prow < a.M) {
+          {
             float old[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) old[j] = (c0 + j < a.r) ? P[(long long)(c0 + j) * a.M + prow] : 0.f;
+            for (int j = 0; j < 16; ++j) old[j] = (c0 + j < a.r) ? P[(long long)(c0 + j) * a.pstride + prow] : 0.f;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              if (c0 + j < a.r) P[(long long)(c0 + j) * a.M + prow] = old[j] + acc[j];
+              if (c0 + j < a.r) P[(long long)(c0 + j) * a.pstride + prow] = old[j] + acc[j];
           }
         }
       }
@@ -280,7 +287,7 @@ cudaError_t launch_kp(const GemmArgs& a, cudaStream_t s) {
   const int by_smem = (int)((228 * 1024) / (smem + 1024));
   const int by_tmem = 512 / ncols;
   const int occ = std::max(1, std::min(std::min(by_regs, by_smem), std::min(by_tmem, 8)));
-  const long long ntiles = (a.M + TILE_M - 1) / TILE_M;
+  const long long ntiles = (long long)a.L.nz * a.L.ny * ((a.L.nx + TILE_M - 1) / TILE_M);
   const long long grid_x = std::min<long long>(ntiles, (long long)sms * occ);
   dim3 grid((unsigned)grid_x, a.nshots);
   probe_gemm_tf32<KP, PC><<<grid, TILE_M, smem, s>>>(a, NP, ncols, ntiles);

@@ -10,9 +10,11 @@ namespace tp {
 // Halo width of every padded field in y and z: zero layers around the grid
 // that make the Dirichlet boundary of the Laplacian free (radius R <= 4).
 constexpr int H = 4;
-// x halo: 8 zero columns, so that every row's interior starts on a 32-byte
-// DRAM sector (rows are 64-byte multiples); x0 - 4 boxes stay 16-byte aligned.
-constexpr int HX = 8;
+// x halo: 32 zero columns, so that every row's interior starts on a 128-byte
+// L2 line (row pitch a multiple of 32 floats).  Partial-line writes make the
+// L2 fetch the rest of the line from DRAM; aligned rows avoid those fills.
+// The right halo of a row is the left padding of the next row.
+constexpr int HX = 32;
 // x extents are padded to a multiple of this (tile widths of the sweeps).
 constexpr int XALIGN = 128;
 // y extents (3-D) are padded to a multiple of this.
@@ -25,7 +27,7 @@ struct Layout {
   int ndim, nx, ny, nz;
   int px, py, pz;       // padded extents (py = 1 in 2-D)
   long long plane;      // py * px
-  long long field;      // pz * plane, rounded up to 64 floats (256 B)
+  long long field;      // pz * plane + slack, rounded up to 64 floats (256 B)
   __host__ __device__ long long off(long long z, long long y, long long x) const {
     return (z + H) * plane + (y + (ndim == 3 ? H : 0)) * px + (x + HX);
   }
@@ -78,11 +80,15 @@ cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const St
 // P[s][i][x] += sum_{k < nlev} ring[s][(level0 + k) mod nslots][x] * Q[s][level0 + k + qshift][i]
 // with Q rows outside [qlo, qhi] read as zero.  tcgen05 (kind::tf32) with a
 // hi/lo split of the snapshots (and of Q when q_has_lo).
+// The GEMM walks interior row segments of 128 points: M = nz * ny * nxt * 128
+// with nxt = ceil(nx / 128); padding columns beyond nx inside a segment are
+// zero in both operands and stay zero.
 struct GemmArgs {
+  Layout L;
   const float* ring; long long slot_stride; long long ring_ss; int nslots;
   int level0, nlev, qshift, qlo, qhi;
   const float* Q; int nt, r; long long q_ss;
-  float* P; long long M; long long p_ss;
+  float* P; long long pstride; long long p_ss;  // P[s][i] at P + s*p_ss + i*pstride
   int nshots;
   int q_has_lo;
   int* err;

@@ -52,8 +52,8 @@ def test_workspace_sizes_follow_the_memory_model(L):
     full = native.tp_workspace_bytes(native.OP_GRADIENT_FULL, g, geo)
     probed = native.tp_workspace_bytes(native.OP_GRADIENT_PROBED, g, geo, pr)
     N, nt = w.N, w.nt
-    # full storage holds the N x nt history (padded layout adds < 15 %)
-    assert 4 * N * nt <= full <= 1.15 * 4 * N * nt + 2 * 4 * w.nt * w.nrec + (1 << 30)
+    # full storage holds the N x nt history (padded layout adds < 25 %)
+    assert 4 * N * nt <= full <= 1.25 * 4 * N * nt + 2 * 4 * w.nt * w.nrec + (1 << 30)
     # probed: 2 N r accumulators + (T + 2) ring levels (+ padding), >= 10x less
     assert probed >= 4 * N * (2 * 32 + 34)
     assert full / probed >= 10.0
