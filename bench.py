@@ -246,9 +246,11 @@ def main():
     avg_gemm_ms = gm["ms"] / max(gm["launches"], 1)
     # algorithmic bytes of one window GEMM: T snapshots read + r accumulators read and written
     from paper_2104_00794_gb300.native import tp_probe  # noqa: F401
-    field = (w.nz + 8) * ((w.ny + 15) // 16 * 16 + 8) * ((w.nx + 127) // 128 * 128 + 8)
-    gemm_bytes = field * 4 * (w.T + 2 * w.r)
-    gemm_flops = 2.0 * field * w.T * w.r * 2  # hi and lo products (Rademacher probes exact in tf32)
+    # the GEMM walks interior row segments of 128 points: T snapshots read,
+    # r accumulators read and written per point
+    gemm_pts = w.nz * w.ny * ((w.nx + 127) // 128 * 128)
+    gemm_bytes = gemm_pts * 4 * (w.T + 2 * w.r)
+    gemm_flops = 2.0 * gemm_pts * w.T * w.r * 2  # hi and lo products (Rademacher probes exact in tf32)
     launches = sum(v["launches"] for v in kern.values())
 
     # ---- full-storage gradient of the same problem

@@ -19,6 +19,8 @@
 // is accurate to a few 1e-7 relative; Rademacher / identity probes are exact
 // in tf32 and skip the third MMA.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "tp_internal.h"
 
@@ -267,6 +269,257 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
   }
 }
 
+// ------------------------------------------------------------------ TMA variant
+// For r <= 32: a producer warp streams each tile's window rows (nlev x 512 B)
+// and old accumulator rows (r x 512 B) into a 2-stage shared-memory ring with
+// cp.async.bulk (completion counted on an mbarrier); four worker warps split
+// the snapshots into tf32 hi/lo operands, one thread issues the MMAs, and the
+// workers add the TMEM tile to the staged accumulators and store them.  Two
+// CTAs per SM (KP = 32) keep four tiles of copies in flight per SM without
+// holding them in registers.
+constexpr int GNS = 2;      // stages
+constexpr int GRP = 32;     // accumulator rows staged per tile (r <= 32)
+constexpr int GW = 4;       // worker warps
+constexpr int GTHREADS = (GW + 1) * 32;
+
+__device__ __forceinline__ void mbar_init(uint32_t b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_abort(uint32_t bar, uint32_t phase, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+template <int KP>
+struct GCfg {
+  static constexpr uint32_t STAGE = (uint32_t)(KP + GRP) * TILE_M * 4;  // A rows then P rows
+  static constexpr uint32_t ABYTES = TILE_M * KP * 4;
+  static constexpr uint32_t BBYTES = GRP * KP * 4;
+  static constexpr size_t SMEM = (size_t)GNS * STAGE + 2 * ABYTES + 2 * BBYTES + 8 * (2 * GNS + 1) + 32;
+};
+
+template <int KP>
+__global__ void __launch_bounds__(GTHREADS)
+probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
+  using C = GCfg<KP>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* stage0 = smem;
+  unsigned char* A_hi = smem + GNS * C::STAGE;
+  unsigned char* A_lo = A_hi + C::ABYTES;
+  unsigned char* B_hi = A_lo + C::ABYTES;
+  unsigned char* B_lo = B_hi + C::BBYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(B_lo + C::BBYTES);
+  const uint32_t full = smem_u32(bars), empty = full + 8 * GNS, mma_bar = empty + 8 * GNS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * GNS + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int shot = blockIdx.y;
+  const float* ring = a.ring + shot * a.ring_ss;
+  const float* Q = a.Q + shot * a.q_ss;
+  float* P = a.P + shot * a.p_ss;
+  const int nxt = (a.L.nx + TILE_M - 1) / TILE_M;
+  auto tile_base = [&](long long tile) -> long long {
+    const long long row = tile / nxt;
+    return a.L.off(row / a.L.ny, row % a.L.ny, (long long)(tile % nxt) * TILE_M);
+  };
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(32));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < GNS; ++s) {
+      mbar_init(full + 8 * s, 1);
+      mbar_init(empty + 8 * s, GW);
+    }
+    mbar_init(mma_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // B operand (probe block) once per CTA, as in probe_gemm_tf32
+  for (int e = tid; e < NP * KP; e += GTHREADS) {
+    const int n = e / KP, k = e % KP;
+    const int row = a.level0 + k + a.qshift;
+    float v = 0.f;
+    if (n < a.r && k < a.nlev && row >= a.qlo && row <= a.qhi) v = Q[(long long)row * a.r + n];
+    const float hi = tf32_hi(v);
+    *reinterpret_cast<float*>(B_hi + kmaj_off(n, k, KP)) = hi;
+    *reinterpret_cast<float*>(B_lo + kmaj_off(n, k, KP)) = v - hi;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int slot0 = a.level0 % a.nslots;
+
+  if (warp == GW) {
+    // ------------------------------------------------------------ producer warp
+    const uint32_t bytes = (uint32_t)(a.nlev + a.r) * TILE_M * 4;
+    bool ok = true;
+    uint32_t it = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int s = it % GNS;
+      if (it >= (uint32_t)GNS) {
+        bool w = true;
+        if (lane == 0) w = mbar_wait_abort(empty + 8 * s, ((it / GNS) - 1) & 1, abort_flag);
+        if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) { ok = false; break; }
+      }
+      if (lane == 0) mbar_expect_tx(full + 8 * s, bytes);
+      __syncwarp();
+      const long long base = tile_base(tile);
+      const uint32_t dst = smem_u32(stage0 + s * C::STAGE);
+      for (int c = lane; c < a.nlev + a.r; c += 32) {
+        const float* src;
+        uint32_t d;
+        if (c < a.nlev) {
+          const int sl = slot0 + c >= a.nslots ? slot0 + c - a.nslots : slot0 + c;
+          src = ring + (long long)sl * a.slot_stride + base;
+          d = dst + (uint32_t)c * TILE_M * 4;
+        } else {
+          src = P + (long long)(c - a.nlev) * a.pstride + base;
+          d = dst + (uint32_t)(KP + c - a.nlev) * TILE_M * 4;
+        }
+        bulk_g2s(d, src, TILE_M * 4, full + 8 * s);
+      }
+    }
+    if (!ok && lane == 0) atomicOr(a.err, 1);
+    // drain: every issued stage must have landed before the CTA exits
+    if (lane == 0) {
+      for (uint32_t j = (it > (uint32_t)GNS ? it - GNS : 0); j < it; ++j) {
+        const long long t0 = clock64();
+        while (!mbar_wait_abort(full + 8 * (j % GNS), (j / GNS) & 1, abort_flag) && clock64() - t0 < WAIT_CYCLES) {}
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ workers
+    const uint32_t idesc = idesc_tf32(TILE_M, NP);
+    const uint32_t sbo = KP * 32, lbo = 128;
+    const uint32_t a_hi_u = smem_u32(A_hi), a_lo_u = smem_u32(A_lo);
+    const uint32_t b_hi_u = smem_u32(B_hi), b_lo_u = smem_u32(B_lo);
+    uint32_t it = 0, mph = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+      const int s = it % GNS;
+      if (!mbar_wait_abort(full + 8 * s, (it / GNS) & 1, abort_flag)) { ok = false; }
+      bar_named(1, GW * 32);
+      if (*abort_flag) { ok = false; break; }
+      const float* sA = reinterpret_cast<const float*>(stage0 + s * C::STAGE);
+      const float* sP = sA + KP * TILE_M;
+      // 1. split this thread's point column of the staged snapshots
+#pragma unroll
+      for (int k4 = 0; k4 < KP; k4 += 4) {
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = (k4 + j < a.nlev) ? sA[(k4 + j) * TILE_M + tid] : 0.f;
+        float4 hi, lo;
+        hi.x = tf32_hi(v[0]); hi.y = tf32_hi(v[1]); hi.z = tf32_hi(v[2]); hi.w = tf32_hi(v[3]);
+        lo.x = v[0] - hi.x; lo.y = v[1] - hi.y; lo.z = v[2] - hi.z; lo.w = v[3] - hi.w;
+        const uint32_t o = kmaj_off(tid, k4, KP);
+        *reinterpret_cast<float4*>(A_hi + o) = hi;
+        *reinterpret_cast<float4*>(A_lo + o) = lo;
+      }
+      // 2. old accumulators of this point, then release the stage
+      float pold[GRP];
+#pragma unroll
+      for (int i = 0; i < GRP; ++i) pold[i] = i < a.r ? sP[i * TILE_M + tid] : 0.f;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + 8 * s);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      bar_named(1, GW * 32);
+      // 3. MMAs
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int kk = 0; kk < KP / 8; ++kk) {
+          const uint32_t ko = kk * 2 * 128;
+          const uint64_t ah = smem_desc(a_hi_u + ko, lbo, sbo), al = smem_desc(a_lo_u + ko, lbo, sbo);
+          const uint64_t bh = smem_desc(b_hi_u + ko, lbo, sbo), bl = smem_desc(b_lo_u + ko, lbo, sbo);
+          mma_tf32(tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
+          mma_tf32(tmem, al, bh, idesc, 1u);
+          if (a.q_has_lo) mma_tf32(tmem, ah, bl, idesc, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mma_bar)
+                     : "memory");
+      }
+      // 4. epilogue
+      int done = 1;
+      if (tid == 0) done = mbar_wait_abort(mma_bar, mph, abort_flag) ? 1 : 0;
+      mph ^= 1u;
+      bar_named(1, GW * 32);
+      if (*abort_flag || !done) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const long long prow = tile_base(tile) + tid;
+      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+      for (int c = 0; c < GRP / 16; ++c) {
+        if (c * 16 < NP) {
+          float acc[16];
+          tmem_ld16(trow + (uint32_t)(c * 16), acc);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c * 16 + j < a.r) P[(long long)(c * 16 + j) * a.pstride + prow] = pold[c * 16 + j] + acc[j];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    if (!ok && tid == 0) atomicOr(a.err, 1);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+  }
+}
+
+template <int KP>
+cudaError_t launch_tma(const GemmArgs& a, cudaStream_t s) {
+  using C = GCfg<KP>;
+  const int NP = std::max(16, (a.r + 15) / 16 * 16);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(probe_gemm_tma<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    attr = true;
+  }
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int occ = std::max(1, std::min(4, (int)((228 * 1024) / (C::SMEM + 1024))));
+  const long long ntiles = (long long)a.L.nz * a.L.ny * ((a.L.nx + TILE_M - 1) / TILE_M);
+  const long long grid_x = std::min<long long>(ntiles, (long long)sms * occ);
+  dim3 grid((unsigned)grid_x, a.nshots);
+  probe_gemm_tma<KP><<<grid, GTHREADS, C::SMEM, s>>>(a, NP, ntiles);
+  return cudaGetLastError();
+}
+
 template <int KP, int PC>
 cudaError_t launch_kp(const GemmArgs& a, cudaStream_t s) {
   const int NP = std::max(16, (a.r + 15) / 16 * 16);
@@ -301,9 +554,18 @@ int gemm_kpad(int T) { return T <= 32 ? 32 : 64; }
 cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
   if (a.nlev <= 0) return cudaSuccess;
   prof_before(2, s);  // TP_KERNEL_PROBE_GEMM
+  static const int variant = [] {  // TP_PROBE_GEMM=regs selects the register-staged kernel
+    const char* e = getenv("TP_PROBE_GEMM");
+    return (e && strcmp(e, "regs") == 0) ? 1 : 0;
+  }();
   cudaError_t e;
-  if (a.nlev <= 32) e = a.r <= 16 ? launch_kp<32, 16>(a, s) : (a.r <= 32 ? launch_kp<32, 32>(a, s) : launch_kp<32, 0>(a, s));
-  else e = a.r <= 16 ? launch_kp<64, 16>(a, s) : (a.r <= 32 ? launch_kp<64, 32>(a, s) : launch_kp<64, 0>(a, s));
+  if (a.r <= GRP && variant == 0) {
+    e = a.nlev <= 32 ? launch_tma<32>(a, s) : launch_tma<64>(a, s);
+  } else if (a.nlev <= 32) {
+    e = a.r <= 16 ? launch_kp<32, 16>(a, s) : (a.r <= 32 ? launch_kp<32, 32>(a, s) : launch_kp<32, 0>(a, s));
+  } else {
+    e = a.r <= 16 ? launch_kp<64, 16>(a, s) : (a.r <= 32 ? launch_kp<64, 32>(a, s) : launch_kp<64, 0>(a, s));
+  }
   prof_after(2, s);
   return e;
 }
