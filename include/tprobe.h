@@ -144,6 +144,23 @@ tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float
  * TP_PROBE_USER it copies the caller's Z. */
 tp_status tp_probes(const tp_probe* probe, int nt, int shot, float* Z, void* stream);
 
+/* Data misfit J = 1/2 sum_i (d_syn[i] - d_obs[i])^2 over n samples, written
+ * to the DEVICE double *misfit, computed without any workspace.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate
+ * device memory where they need the misfit -- code that gets all of its device
+ * memory from a host framework's own pool and may not allocate by itself, or a
+ * latency-critical loop where an allocation (and the synchronisation it can
+ * bring) is not acceptable.  Its scratch (one fp64 partial per 65536 samples)
+ * is a fixed 32 KiB array inside the library, held on every GPU that loads the
+ * library until the process exits; so n may be at most 268,435,456 samples
+ * (TP_ERR_ARG beyond).  The first call on a device looks the array up on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race and must
+ * be ordered by the caller.  d_syn, d_obs: device float arrays of n samples
+ * (any layout, e.g. [nshots][nt][nrec]).  Errors: TP_ERR_ARG (NULL pointer,
+ * n < 1 or too large), TP_ERR_CUDA (lookup or launch failed). */
+tp_status tp_misfit_noalloc(const float* d_syn, const float* d_obs, int64_t n, double* misfit, void* stream);
+
 /* Synchronises `stream` and reports whether a bounded device-side wait in
  * the last call on this workspace gave up (TP_ERR_TIMEOUT) or not (TP_OK);
  * clears the flag. */

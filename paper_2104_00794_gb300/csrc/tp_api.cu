@@ -77,6 +77,8 @@ void prof_after(int, cudaStream_t s) {
   g_prof.open = false;
 }
 
+void set_last_error(const char* msg) { g_err = msg; }
+
 Layout make_layout(int ndim, int nx, int ny, int nz) {
   Layout L;
   L.ndim = ndim;

@@ -143,6 +143,9 @@ cudaError_t launch_source_term(const Layout& L, const float* vel, const int64_t*
                                const float* qbar, const float* V, int r, long long v_ss,
                                const double* srcacc, float* grad, cudaStream_t s);
 
+// message returned by tp_last_error() on the calling thread
+void set_last_error(const char* msg);
+
 // ---------------------------------------------------------------- profiling
 void prof_before(int kind, cudaStream_t s);
 void prof_after(int kind, cudaStream_t s);

@@ -67,13 +67,14 @@ def lib():
         L.tp_gradient_full.argtypes = [G, E, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.tp_probes.argtypes = [Pr, i32, i32, vp, vp]
         L.tp_workspace_status.argtypes = [vp, sz, vp]
+        L.tp_misfit_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
         L.tp_last_error.restype = ctypes.c_char_p
         L.tp_profile_begin.argtypes = [i32]
         L.tp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         L.tp_kernel_name.argtypes = [i32]
         L.tp_kernel_name.restype = ctypes.c_char_p
         for f in ("tp_forward", "tp_adjoint", "tp_gradient_probed", "tp_gradient_full", "tp_probes",
-                  "tp_workspace_status", "tp_profile_begin", "tp_profile_end"):
+                  "tp_workspace_status", "tp_profile_begin", "tp_profile_end", "tp_misfit_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
         return L
@@ -117,6 +118,13 @@ def tp_gradient_full(grid, geom, vel, wavelet, d_obs, grad, misfit, gnorm, ws, w
 
 def tp_probes(probe, nt, shot, Z, stream):
     _check(lib().tp_probes(ctypes.byref(probe), nt, shot, Z, stream))
+
+
+def tp_misfit_noalloc(d_syn, d_obs, n, misfit, stream):
+    """J = 1/2 sum (d_syn - d_obs)^2 into the device double at `misfit`,
+    using the library's fixed scratch instead of a workspace (for callers
+    that cannot allocate device memory at that point)."""
+    _check(lib().tp_misfit_noalloc(d_syn, d_obs, n, misfit, stream))
 
 
 def tp_workspace_status(ws, ws_bytes, stream):
