@@ -63,8 +63,19 @@ typedef enum {
   TP_OP_FORWARD = 0,
   TP_OP_ADJOINT = 1,
   TP_OP_GRADIENT_PROBED = 2,
-  TP_OP_GRADIENT_FULL = 3
+  TP_OP_GRADIENT_FULL = 3,
+  TP_OP_PROBED_FORWARD = 4,   /* tp_probed_forward's transient workspace */
+  TP_OP_PROBED_BACKWARD = 5   /* tp_probed_backward's transient workspace */
 } tp_op;
+
+/* Storage of the probe accumulators (ubar, vbar); the accumulation itself is
+ * always fp32 (the tensor-core tile is added in fp32 before it is stored). */
+typedef enum {
+  TP_ACC_F32 = 0,         /* fp32: 4 B per value */
+  TP_ACC_BF16 = 1,        /* bf16, round to nearest: 2 B per value */
+  TP_ACC_BF16_KAHAN = 2   /* bf16 value + bf16 compensation (the rounding error of
+                             the stored value, carried to the next window): 4 B */
+} tp_acc;
 
 /* Grid and time axis.  Eq. 2 (F(m; q) on this grid). */
 typedef struct {
@@ -98,11 +109,12 @@ typedef struct {
   const float* Z_user; /* device [nshots][nt][r] when kind == TP_PROBE_USER */
   float scale;         /* estimator scale; 0 selects the default: 1/r for
                           random probes (Eq. 1), 1 for IDENTITY and USER */
+  int acc;             /* tp_acc storage of the accumulators; BF16 kinds need r <= 32 */
 } tp_probe;
 
 /* Bytes of device workspace that `op` needs (0 on invalid arguments; see
- * tp_last_error).  `probe` is read only for TP_OP_GRADIENT_PROBED.  The
- * workspace must be 256-byte aligned. */
+ * tp_last_error).  `probe` is read only for the probed ops.  The workspace
+ * must be 256-byte aligned. */
 size_t tp_workspace_bytes(int op, const tp_grid* grid, const tp_geom* geom, const tp_probe* probe);
 
 /* Forward modelling d = F(m; q) (Eq. 2; Algorithm 1 lines 0-3 without the
@@ -138,6 +150,30 @@ tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_
 tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float* vel,
                            const float* wavelet, const float* d_obs, float* grad, double* misfit,
                            double* gnorm, void* ws, size_t ws_bytes, void* stream);
+
+/* Algorithm 1 split at the residual, for callers that drive the adjoint
+ * source themselves (e.g. a torch.autograd.Function whose backward receives
+ * dL/dd).  `state` is a caller-owned device buffer of tp_probed_state_bytes()
+ * (256-byte aligned) holding what must survive between the two halves: the
+ * probes Q and the forward accumulators ubar (2 N r values with vbar, Section
+ * "Memory estimates"); nothing else is kept.
+ *
+ * tp_probed_forward: lines 0-3.  d_out [nshots][nt][nrec] = F(m; q) and ubar
+ * into `state`.  ws: tp_workspace_bytes(TP_OP_PROBED_FORWARD, ...).
+ * tp_probed_backward: lines 4-8 with adjoint source adj_src [nshots][nt][nrec]
+ * (for J = 1/2 |d - d_obs|^2 that is the residual).  grad [nz][ny][nx]
+ * receives dJ/dm (wrt_velocity = 0) or dJ/dv = dJ/dm * (-2 / v^3)
+ * (wrt_velocity = 1); gnorm (optional, device) its fp64 norm.
+ * ws: tp_workspace_bytes(TP_OP_PROBED_BACKWARD, ...).  The same grid, geom,
+ * probe and vel must be passed to both halves. */
+size_t tp_probed_state_bytes(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe);
+tp_status tp_probed_forward(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe,
+                            const float* vel, const float* wavelet, float* d_out, void* state,
+                            size_t state_bytes, void* ws, size_t ws_bytes, void* stream);
+tp_status tp_probed_backward(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe,
+                             const float* vel, const float* wavelet, const float* adj_src,
+                             int wrt_velocity, float* grad, double* gnorm, void* state,
+                             size_t state_bytes, void* ws, size_t ws_bytes, void* stream);
 
 /* The probing matrix that tp_gradient_probed draws for shot `shot`
  * (Eq. 1 probes from SplitMix64; Z[t][i], [nt][r], unscaled).  For

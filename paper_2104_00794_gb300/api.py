@@ -44,10 +44,12 @@ class ProbeSpec:
     seed: int = 2104
     scale: float = 0.0
     Z_user: Optional[torch.Tensor] = None
+    acc: str = "f32"  # accumulator storage: "f32", "bf16", "bf16_kahan"
 
     def to_c(self) -> native.tp_probe:
         return native.tp_probe(native.PROBE_KINDS[self.kind], int(self.r), int(self.T), int(self.seed) & (2**64 - 1),
-                               _ptr(self.Z_user) if self.Z_user is not None else None, float(self.scale))
+                               _ptr(self.Z_user) if self.Z_user is not None else None, float(self.scale),
+                               native.ACC_TYPES[self.acc])
 
 
 class Problem:
@@ -147,6 +149,41 @@ class Problem:
         native.tp_gradient_full(self.grid, self.geom, _ptr(vel), _ptr(wavelet), _ptr(d_obs), _ptr(grad),
                                 scalars.data_ptr(), scalars.data_ptr() + 8, ws, n, _stream())
         return grad, scalars
+
+    # ------------------------------------------------------------ split Algorithm 1
+    def state_bytes(self, probe: ProbeSpec) -> int:
+        return native.tp_probed_state_bytes(self.grid, self.geom, probe.to_c())
+
+    def new_state(self, probe: ProbeSpec) -> torch.Tensor:
+        """Caller-owned, 256-byte aligned buffer for the probes and forward accumulators."""
+        n = self.state_bytes(probe)
+        buf = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+        off = (-buf.data_ptr()) % 256
+        return buf[off:off + n]
+
+    def probed_forward(self, vel, wavelet, probe: ProbeSpec, state: torch.Tensor, d_out=None):
+        """d = F(m; q) and the forward probe accumulators into `state` (Algorithm 1 lines 0-3)."""
+        vel, wavelet = _f32(vel, self.device), _f32(wavelet, self.device)
+        if d_out is None:
+            d_out = torch.empty((self.nshots, self.nt, self.geom.nrec), dtype=torch.float32, device=self.device)
+        ws, n = self.workspace(native.OP_PROBED_FORWARD, probe)
+        native.tp_probed_forward(self.grid, self.geom, probe.to_c(), _ptr(vel), _ptr(wavelet), _ptr(d_out),
+                                 state.data_ptr(), state.numel(), ws, n, _stream())
+        return d_out
+
+    def probed_backward(self, vel, wavelet, adj_src, probe: ProbeSpec, state: torch.Tensor, wrt_velocity=False,
+                        grad=None, gnorm=None):
+        """Gradient (dJ/dm, or dJ/dv) from the adjoint source and `state` (Algorithm 1 lines 4-8)."""
+        vel, wavelet, adj_src = _f32(vel, self.device), _f32(wavelet, self.device), _f32(adj_src, self.device)
+        if grad is None:
+            grad = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        if gnorm is None:
+            gnorm = torch.empty(1, dtype=torch.float64, device=self.device)
+        ws, n = self.workspace(native.OP_PROBED_BACKWARD, probe)
+        native.tp_probed_backward(self.grid, self.geom, probe.to_c(), _ptr(vel), _ptr(wavelet), _ptr(adj_src),
+                                  1 if wrt_velocity else 0, _ptr(grad), gnorm.data_ptr(), state.data_ptr(),
+                                  state.numel(), ws, n, _stream())
+        return grad, gnorm
 
     def probes(self, probe: ProbeSpec, shot: int = 0, nt: Optional[int] = None):
         nt = self.nt if nt is None else nt

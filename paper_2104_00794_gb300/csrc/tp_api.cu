@@ -119,12 +119,17 @@ struct Plan {
   int op = 0;
   Layout L{};
   Weights W{};
-  int nshots = 0, nsrc = 0, nrec = 0, nt = 0, r = 0, T = 0, S = 0, kind = 0;
+  int nshots = 0, nsrc = 0, nrec = 0, nt = 0, r = 0, T = 0, S = 0, kind = 0, acc = 0;
   float scale = 1.f;
   size_t bytes = 0;
   size_t o_scal = 0, o_part = 0, o_c2 = 0, o_f = 0, o_P = 0, o_V = 0, o_Q = 0, o_d = 0, o_soff = 0, o_roff = 0,
-         o_cs = 0, o_cr = 0, o_qbar = 0, o_gacc = 0, o_sacc = 0;
+         o_cs = 0, o_cr = 0, o_qbar = 0, o_gacc = 0, o_sacc = 0, o_conv = 0;
   long long nf = 0;  // fields in the wavefield block
+  // probed state (Q, then the forward accumulators): offsets inside the state
+  // buffer, which tp_gradient_probed places at o_state of its workspace
+  size_t s_Q = 0, s_P = 0, state_bytes = 0, o_state = 0;
+  long long acc_elems = 0;  // accumulator storage elements per shot (r fields, 2r with compensation)
+  size_t acc_esize = 4;     // bytes per stored element
 };
 
 size_t take(size_t& cur, size_t bytes) {
@@ -158,6 +163,8 @@ tp_status check_geom(const tp_geom* g) {
 
 tp_status check_probe(const tp_probe* p, int nt) {
   if (!p) return fail(TP_ERR_ARG, "probe is NULL");
+  if (p->acc < TP_ACC_F32 || p->acc > TP_ACC_BF16_KAHAN) return fail(TP_ERR_ARG, "unknown accumulator type %d", p->acc);
+  if (p->acc != TP_ACC_F32 && p->r > 32) return fail(TP_ERR_ARG, "bf16 accumulators need r <= 32 (got %d)", p->r);
   if (p->kind < 0 || p->kind > 3) return fail(TP_ERR_ARG, "unknown probe kind %d", p->kind);
   if (p->r < 1 || p->r > 256) return fail(TP_ERR_ARG, "r must be in 1..256 (got %d)", p->r);
   if (p->kind == TP_PROBE_IDENTITY && p->r != nt) return fail(TP_ERR_ARG, "identity probes need r == nt");
@@ -171,8 +178,9 @@ tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe
   tp_status st = check_grid(g);
   if (st != TP_OK) return st;
   if ((st = check_geom(geo)) != TP_OK) return st;
-  if (op < TP_OP_FORWARD || op > TP_OP_GRADIENT_FULL) return fail(TP_ERR_ARG, "unknown op %d", op);
-  if (op == TP_OP_GRADIENT_PROBED && (st = check_probe(pr, g->nt)) != TP_OK) return st;
+  if (op < TP_OP_FORWARD || op > TP_OP_PROBED_BACKWARD) return fail(TP_ERR_ARG, "unknown op %d", op);
+  const bool probed = op == TP_OP_GRADIENT_PROBED || op == TP_OP_PROBED_FORWARD || op == TP_OP_PROBED_BACKWARD;
+  if (probed && (st = check_probe(pr, g->nt)) != TP_OK) return st;
   P->op = op;
   P->L = make_layout(g->ndim, g->nx, g->ny, g->nz);
   P->W = stencil_weights(g->order);
@@ -196,21 +204,35 @@ tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe
       P->nf = 3 * ns;
       P->o_f = take(cur, (size_t)P->nf * fb);
       break;
-    case TP_OP_GRADIENT_PROBED: {
+    case TP_OP_GRADIENT_PROBED:
+    case TP_OP_PROBED_FORWARD:
+    case TP_OP_PROBED_BACKWARD: {
       P->kind = pr->kind;
       P->r = pr->r;
       P->T = pr->T;
       P->S = P->T + 2;
+      P->acc = pr->acc;
       P->scale = pr->scale > 0.f ? pr->scale
                                  : ((pr->kind == TP_PROBE_RADEMACHER || pr->kind == TP_PROBE_GAUSSIAN) ? 1.0f / pr->r : 1.0f);
+      P->acc_esize = P->acc == TP_ACC_F32 ? 4 : 2;
+      P->acc_elems = (long long)P->r * P->L.field * (P->acc == TP_ACC_BF16_KAHAN ? 2 : 1);
+      const size_t accb = (size_t)ns * P->acc_elems * P->acc_esize;  // one accumulator set, all shots
+      size_t sc = 0;
+      P->s_Q = take(sc, (size_t)ns * P->nt * P->r * sizeof(float));
+      P->s_P = take(sc, accb);
+      P->state_bytes = sc;
       P->nf = (long long)P->S * ns;
-      P->o_f = take(cur, (size_t)P->nf * fb);
-      P->o_P = take(cur, (size_t)ns * P->r * fb);
-      P->o_V = take(cur, (size_t)ns * P->r * fb);
-      P->o_Q = take(cur, (size_t)ns * P->nt * P->r * sizeof(float));
-      P->o_d = take(cur, (size_t)ns * P->nt * P->nrec * sizeof(float));
-      P->o_qbar = take(cur, (size_t)ns * P->nsrc * P->r * sizeof(float));
-      P->o_gacc = take(cur, (size_t)ns * fb);
+      P->o_f = take(cur, (size_t)P->nf * fb);  // ring of T+2 levels
+      if (op != TP_OP_PROBED_FORWARD) {
+        P->o_V = take(cur, accb);
+        P->o_qbar = take(cur, (size_t)ns * P->nsrc * P->r * sizeof(float));
+        P->o_gacc = take(cur, (size_t)ns * fb);
+        if (P->acc != TP_ACC_F32) P->o_conv = take(cur, (size_t)2 * ns * fb);  // fp32 copies of P_i, V_i
+      }
+      if (op == TP_OP_GRADIENT_PROBED) {
+        P->o_state = take(cur, P->state_bytes);
+        P->o_d = take(cur, (size_t)ns * P->nt * P->nrec * sizeof(float));
+      }
       break;
     }
     case TP_OP_GRADIENT_FULL:
@@ -423,38 +445,40 @@ tp_status tp_adjoint(const tp_grid* grid, const tp_geom* geom, const float* vel,
   return TP_OK;
 }
 
-tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe, const float* vel,
-                             const float* wavelet, const float* d_obs, float* grad, double* misfit, double* gnorm,
-                             void* ws, size_t ws_bytes, void* stream) {
-  Plan P;
-  TRYS(make_plan(TP_OP_GRADIENT_PROBED, grid, geom, probe, &P));
-  TRYS(check_ws(P, ws, ws_bytes));
-  if (!wavelet || !d_obs || !grad) return fail(TP_ERR_ARG, "wavelet/d_obs/grad is NULL");
-  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
-  TRYS(setup(c, grid, geom, vel));
-  const size_t fb = (size_t)P.L.field * sizeof(float);
-  const int nt = P.nt, T = P.T, S = P.S, r = P.r;
-  const long long ring_ss = (long long)S * P.L.field;
-  TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));
-  TRY(cudaMemsetAsync(c.at<float>(P.o_P), 0, (size_t)P.nshots * r * fb, c.st));
-  TRY(cudaMemsetAsync(c.at<float>(P.o_V), 0, (size_t)P.nshots * r * fb, c.st));
-  TRY(cudaMemsetAsync(c.at<float>(P.o_gacc), 0, (size_t)P.nshots * fb, c.st));
-  float* d = c.at<float>(P.o_d);
-  TRY(cudaMemsetAsync(d, 0, (size_t)P.nshots * nt * P.nrec * sizeof(float), c.st));
-  float* Q = c.at<float>(P.o_Q);
-  TRY(launch_probes(P.kind, nt, r, probe->seed, 0, P.nshots, probe->Z_user, Q, c.st));
-  const Fam ring{P.o_f, (int)P.nf, S};
-  auto level = [S](int t) { return t % S; };
+}  // extern "C"
 
+namespace tp {
+namespace {
+
+GemmArgs gemm_args(const Ctx& c, float* Q) {
+  const Plan& P = c.P;
   GemmArgs g{};
-  g.ring = c.at<float>(P.o_f); g.slot_stride = P.L.field; g.ring_ss = ring_ss; g.nslots = S;
-  g.Q = Q; g.nt = nt; g.r = r; g.q_ss = (long long)nt * r;
-  g.L = P.L; g.pstride = P.L.field; g.nshots = P.nshots; g.qlo = 2; g.qhi = nt - 1;
+  g.ring = c.at<float>(P.o_f); g.slot_stride = P.L.field; g.ring_ss = (long long)P.S * P.L.field; g.nslots = P.S;
+  g.Q = Q; g.nt = P.nt; g.r = P.r; g.q_ss = (long long)P.nt * P.r;
+  g.L = P.L; g.pstride = P.L.field; g.p_ss = P.acc_elems; g.acc = P.acc;
+  g.nshots = P.nshots; g.qlo = 2; g.qhi = P.nt - 1;
   g.q_has_lo = (P.kind == TP_PROBE_GAUSSIAN || P.kind == TP_PROBE_USER) ? 1 : 0;
   g.err = c.err();
+  return g;
+}
 
-  // forward: P_s[:, i] = sum_{j=2}^{nt-2} Q_s[j+1, i] u_s[j]  (windows of T levels)
-  g.P = c.at<float>(P.o_P); g.p_ss = (long long)r * P.L.field; g.qshift = 1;
+// Algorithm 1 lines 0-3: forward sweep; d (all shots, zeroed here) receives
+// R u[t]; the accumulators Pacc receive P_i = sum_{j=2}^{nt-2} Q[j+1, i] u[j]
+// (windows of T levels), from which ubar_i = v^2 (L P_i + S^T qbar_i).
+tp_status probed_forward_impl(const Ctx& c, const tp_probe* probe, const float* wavelet, float* d, float* Q,
+                              void* Pacc) {
+  const Plan& P = c.P;
+  const size_t fb = (size_t)P.L.field * sizeof(float);
+  const int nt = P.nt, T = P.T, S = P.S;
+  TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));
+  TRY(cudaMemsetAsync(Pacc, 0, (size_t)P.nshots * P.acc_elems * P.acc_esize, c.st));
+  TRY(cudaMemsetAsync(d, 0, (size_t)P.nshots * nt * P.nrec * sizeof(float), c.st));
+  TRY(launch_probes(P.kind, nt, P.r, probe->seed, 0, P.nshots, probe->Z_user, Q, c.st));
+  const Fam ring{P.o_f, (int)P.nf, S};
+  auto level = [S](int t) { return t % S; };
+  GemmArgs g = gemm_args(c, Q);
+  g.P = Pacc;
+  g.qshift = 1;
   const int jlast = nt - 2;
   auto fwd_after = [&](int lev) -> tp_status {
     if (lev < 2 || lev > jlast) return TP_OK;
@@ -466,14 +490,26 @@ tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_
     }
     return TP_OK;
   };
-  TRYS(forward_loop(c, ring, level, wavelet, d, fwd_after));
-  TRYS(misfit_and_residual(c, d, d_obs, misfit));
+  return forward_loop(c, ring, level, wavelet, d, fwd_after);
+}
 
-  // adjoint: V_s[:, i] = sum_{k=2}^{nt-1} Q_s[k, i] lambda_s[k]  (windows from the top)
-  for (int k = nt; k <= nt + 1; ++k)
-    for (int s = 0; s < P.nshots; ++s)
-      TRY(cudaMemsetAsync(c.ptr(ring, level(k)) + s * ring_ss, 0, fb, c.st));
-  g.P = c.at<float>(P.o_V); g.qshift = 0;
+// Algorithm 1 lines 4-8: adjoint sweep driven by s (all shots), vbar_i =
+// sum_{k=2}^{nt-1} Q[k, i] lambda[k], then grad = -scale sum_i ubar_i vbar_i
+// (dJ/dm, or dJ/dv when wrt_velocity) and its fp64 norm.
+tp_status probed_backward_impl(const Ctx& c, const tp_grid* grid, const tp_geom* geom, const float* vel,
+                               const float* wavelet, const float* s, int wrt_velocity, float* grad, double* gnorm,
+                               const float* Q, const void* Pacc) {
+  const Plan& P = c.P;
+  const size_t fb = (size_t)P.L.field * sizeof(float);
+  const int nt = P.nt, T = P.T, S = P.S, r = P.r;
+  TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));  // levels nt, nt+1 start at zero
+  TRY(cudaMemsetAsync(c.at<char>(P.o_V), 0, (size_t)P.nshots * P.acc_elems * P.acc_esize, c.st));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_gacc), 0, (size_t)P.nshots * fb, c.st));
+  const Fam ring{P.o_f, (int)P.nf, S};
+  auto level = [S](int t) { return t % S; };
+  GemmArgs g = gemm_args(c, const_cast<float*>(Q));
+  g.P = c.at<char>(P.o_V);
+  g.qshift = 0;
   auto adj_after = [&](int lev) -> tp_status {
     const int top = nt - 1 - ((nt - 1 - lev) / T) * T;
     const int bottom = std::max(2, top - T + 1);
@@ -484,22 +520,109 @@ tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_
     }
     return TP_OK;
   };
-  TRYS(adjoint_loop(c, ring, level, d, nullptr, nullptr, nullptr, adj_after));
+  TRYS(adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after));
 
   // combine (Algorithm 1 line 8): ubar = v^2 (L P + S^T qbar), grad = -scale sum_i ubar vbar
-  const long long pss = (long long)r * P.L.field;
-  const Fam fP{P.o_P, (int)(P.nshots * r), r}, fV{P.o_V, (int)(P.nshots * r), r}, fG{P.o_gacc, P.nshots, 1};
-  for (int i = 0; i < r; ++i) {
-    StencilArgs a{c.ref(fP, i), c.ref(fV, i), c.ref(fG, 0), c.ptr(fG, 0), c.ss(fG), P.nshots};
-    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
+  const Fam fG{P.o_gacc, P.nshots, 1};
+  if (P.acc == TP_ACC_F32) {
+    const size_t vo = P.o_V;
+    const long long accf = P.nshots * (long long)r;
+    // the state's accumulators and the workspace's vbar as field families
+    const FieldRef fPr{static_cast<const float*>(Pacc), (int)accf, 0, r};
+    const Fam fV{vo, (int)accf, r};
+    for (int i = 0; i < r; ++i) {
+      FieldRef pi = fPr;
+      pi.f0 = i;
+      StencilArgs a{pi, c.ref(fV, i), c.ref(fG, 0), c.ptr(fG, 0), c.ss(fG), P.nshots};
+      TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
+    }
+  } else {
+    // bf16 storage: fp32 copies of P_i and V_i (per shot) feed the same sweep
+    const Fam fC{P.o_conv, 2 * P.nshots, 1};
+    float* cP = c.ptr(fC, 0);
+    float* cV = c.ptr(fC, P.nshots);
+    for (int i = 0; i < r; ++i) {
+      TRY(launch_acc_to_f32(Pacc, P.acc, r, i, P.L.field, P.nshots, cP, P.L.field, c.st));
+      TRY(launch_acc_to_f32(c.at<char>(P.o_V), P.acc, r, i, P.L.field, P.nshots, cV, P.L.field, c.st));
+      StencilArgs a{c.ref(fC, 0), c.ref(fC, P.nshots), c.ref(fG, 0), c.ptr(fG, 0), c.ss(fG), P.nshots};
+      TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
+    }
   }
   TRY(launch_finish_grad(P.L, vel, c.at<float>(P.o_gacc), P.nshots, P.L.field, P.scale / (grid->h * grid->h), grad,
                          c.st));
   TRY(launch_qbar(Q, nt, r, wavelet, P.nsrc, P.nshots, 1, nt - 2, 1, c.at<float>(P.o_qbar), c.st));
   TRY(launch_source_term(P.L, vel, geom->src, c.at<long long>(P.o_soff), P.nsrc, P.nshots, P.scale,
-                         c.at<float>(P.o_qbar), c.at<float>(P.o_V), r, pss, nullptr, grad, c.st));
+                         c.at<float>(P.o_qbar), c.at<char>(P.o_V), P.acc, r, P.acc_elems, nullptr, grad, c.st));
+  if (wrt_velocity) TRY(launch_chain_velocity(vel, grad, (long long)P.L.nx * P.L.ny * P.L.nz, c.st));
   TRYS(grad_norm(c, grad, gnorm));
   return TP_OK;
+}
+
+tp_status check_state(const Plan& P, void* state, size_t state_bytes) {
+  if (!state) return fail(TP_ERR_ARG, "state is NULL");
+  if (reinterpret_cast<uintptr_t>(state) % 256) return fail(TP_ERR_ARG, "state must be 256-byte aligned");
+  if (state_bytes < P.state_bytes)
+    return fail(TP_ERR_NOMEM, "state of %zu bytes, %zu needed", state_bytes, P.state_bytes);
+  return TP_OK;
+}
+
+}  // namespace
+}  // namespace tp
+
+extern "C" {
+
+tp_status tp_gradient_probed(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe, const float* vel,
+                             const float* wavelet, const float* d_obs, float* grad, double* misfit, double* gnorm,
+                             void* ws, size_t ws_bytes, void* stream) {
+  Plan P;
+  TRYS(make_plan(TP_OP_GRADIENT_PROBED, grid, geom, probe, &P));
+  TRYS(check_ws(P, ws, ws_bytes));
+  if (!wavelet || !d_obs || !grad) return fail(TP_ERR_ARG, "wavelet/d_obs/grad is NULL");
+  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
+  TRYS(setup(c, grid, geom, vel));
+  char* state = c.at<char>(P.o_state);
+  float* Q = reinterpret_cast<float*>(state + P.s_Q);
+  void* Pacc = state + P.s_P;
+  float* d = c.at<float>(P.o_d);
+  TRYS(probed_forward_impl(c, probe, wavelet, d, Q, Pacc));
+  TRYS(misfit_and_residual(c, d, d_obs, misfit));
+  TRYS(probed_backward_impl(c, grid, geom, vel, wavelet, d, 0, grad, gnorm, Q, Pacc));
+  return TP_OK;
+}
+
+size_t tp_probed_state_bytes(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe) {
+  Plan P;
+  if (make_plan(TP_OP_PROBED_FORWARD, grid, geom, probe, &P) != TP_OK) return 0;
+  return P.state_bytes;
+}
+
+tp_status tp_probed_forward(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe, const float* vel,
+                            const float* wavelet, float* d_out, void* state, size_t state_bytes, void* ws,
+                            size_t ws_bytes, void* stream) {
+  Plan P;
+  TRYS(make_plan(TP_OP_PROBED_FORWARD, grid, geom, probe, &P));
+  TRYS(check_ws(P, ws, ws_bytes));
+  TRYS(check_state(P, state, state_bytes));
+  if (!wavelet || !d_out) return fail(TP_ERR_ARG, "wavelet/d_out is NULL");
+  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
+  TRYS(setup(c, grid, geom, vel));
+  char* st = static_cast<char*>(state);
+  return probed_forward_impl(c, probe, wavelet, d_out, reinterpret_cast<float*>(st + P.s_Q), st + P.s_P);
+}
+
+tp_status tp_probed_backward(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe, const float* vel,
+                             const float* wavelet, const float* adj_src, int wrt_velocity, float* grad, double* gnorm,
+                             void* state, size_t state_bytes, void* ws, size_t ws_bytes, void* stream) {
+  Plan P;
+  TRYS(make_plan(TP_OP_PROBED_BACKWARD, grid, geom, probe, &P));
+  TRYS(check_ws(P, ws, ws_bytes));
+  TRYS(check_state(P, state, state_bytes));
+  if (!wavelet || !adj_src || !grad) return fail(TP_ERR_ARG, "wavelet/adj_src/grad is NULL");
+  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
+  TRYS(setup(c, grid, geom, vel));
+  const char* st = static_cast<const char*>(state);
+  return probed_backward_impl(c, grid, geom, vel, wavelet, adj_src, wrt_velocity, grad, gnorm,
+                              reinterpret_cast<const float*>(st + P.s_Q), st + P.s_P);
 }
 
 tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float* vel, const float* wavelet,
@@ -535,7 +658,7 @@ tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float
   TRY(launch_finish_grad(P.L, vel, c.at<float>(P.o_gacc), P.nshots, P.L.field, 1.0f / (grid->h * grid->h), grad,
                          c.st));
   TRY(launch_source_term(P.L, vel, geom->src, c.at<long long>(P.o_soff), P.nsrc, P.nshots, 1.0f, nullptr, nullptr, 0,
-                         0, c.at<double>(P.o_sacc), grad, c.st));
+                         0, 0, c.at<double>(P.o_sacc), grad, c.st));
   TRYS(grad_norm(c, grad, gnorm));
   return TP_OK;
 }

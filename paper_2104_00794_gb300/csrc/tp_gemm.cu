@@ -18,6 +18,8 @@
 // The hi/lo split keeps ~22 significant bits of the snapshots, so the product
 // is accurate to a few 1e-7 relative; Rademacher / identity probes are exact
 // in tf32 and skip the third MMA.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -122,7 +124,7 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
   const int shot = blockIdx.y;
   const float* ring = a.ring + shot * a.ring_ss;
   const float* Q = a.Q + shot * a.q_ss;
-  float* P = a.P + shot * a.p_ss;
+  float* P = static_cast<float*>(a.P) + shot * a.p_ss;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -315,18 +317,21 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 __device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
-template <int KP>
+// ACC: accumulator storage (0 fp32, 1 bf16, 2 bf16 value + bf16 compensation)
+template <int KP, int ACC>
 struct GCfg {
-  static constexpr uint32_t STAGE = (uint32_t)(KP + GRP) * TILE_M * 4;  // A rows then P rows
+  static constexpr uint32_t PROW = ACC == 0 ? TILE_M * 4 : TILE_M * 2;   // bytes of one staged row
+  static constexpr uint32_t PBYTES = GRP * PROW * (ACC == 2 ? 2 : 1);   // accumulator part of a stage
+  static constexpr uint32_t STAGE = (uint32_t)KP * TILE_M * 4 + PBYTES;  // A rows then accumulator rows
   static constexpr uint32_t ABYTES = TILE_M * KP * 4;
   static constexpr uint32_t BBYTES = GRP * KP * 4;
   static constexpr size_t SMEM = (size_t)GNS * STAGE + 2 * ABYTES + 2 * BBYTES + 8 * (2 * GNS + 1) + 32;
 };
 
-template <int KP>
+template <int KP, int ACC>
 __global__ void __launch_bounds__(GTHREADS)
 probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
-  using C = GCfg<KP>;
+  using C = GCfg<KP, ACC>;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stage0 = smem;
   unsigned char* A_hi = smem + GNS * C::STAGE;
@@ -342,7 +347,8 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
   const int shot = blockIdx.y;
   const float* ring = a.ring + shot * a.ring_ss;
   const float* Q = a.Q + shot * a.q_ss;
-  float* P = a.P + shot * a.p_ss;
+  float* Pf = static_cast<float*>(a.P) + shot * a.p_ss;                  // ACC == 0
+  __nv_bfloat16* Ph = static_cast<__nv_bfloat16*>(a.P) + shot * a.p_ss;  // ACC != 0
   const int nxt = (a.L.nx + TILE_M - 1) / TILE_M;
   auto tile_base = [&](long long tile) -> long long {
     const long long row = tile / nxt;
@@ -382,7 +388,8 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
 
   if (warp == GW) {
     // ------------------------------------------------------------ producer warp
-    const uint32_t bytes = (uint32_t)(a.nlev + a.r) * TILE_M * 4;
+    const int ncp = ACC == 2 ? 2 * a.r : a.r;  // accumulator rows copied per tile
+    const uint32_t bytes = (uint32_t)a.nlev * TILE_M * 4 + (uint32_t)ncp * C::PROW;
     bool ok = true;
     uint32_t it = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -396,18 +403,23 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
       __syncwarp();
       const long long base = tile_base(tile);
       const uint32_t dst = smem_u32(stage0 + s * C::STAGE);
-      for (int c = lane; c < a.nlev + a.r; c += 32) {
-        const float* src;
-        uint32_t d;
+      const uint32_t pdst = dst + (uint32_t)KP * TILE_M * 4;
+      for (int c = lane; c < a.nlev + ncp; c += 32) {
         if (c < a.nlev) {
           const int sl = slot0 + c >= a.nslots ? slot0 + c - a.nslots : slot0 + c;
-          src = ring + (long long)sl * a.slot_stride + base;
-          d = dst + (uint32_t)c * TILE_M * 4;
+          bulk_g2s(dst + (uint32_t)c * TILE_M * 4, ring + (long long)sl * a.slot_stride + base, TILE_M * 4, full + 8 * s);
         } else {
-          src = P + (long long)(c - a.nlev) * a.pstride + base;
-          d = dst + (uint32_t)(KP + c - a.nlev) * TILE_M * 4;
+          const int idx = c - a.nlev;
+          if (ACC == 0) {
+            bulk_g2s(pdst + (uint32_t)idx * C::PROW, Pf + (long long)idx * a.pstride + base, C::PROW, full + 8 * s);
+          } else if (ACC == 1 || idx < a.r) {  // bf16 values
+            bulk_g2s(pdst + (uint32_t)idx * C::PROW, Ph + (long long)idx * a.pstride + base, C::PROW, full + 8 * s);
+          } else {                              // bf16 compensations, staged after GRP value rows
+            const int i = idx - a.r;
+            bulk_g2s(pdst + (uint32_t)(GRP + i) * C::PROW, Ph + (long long)(a.r + i) * a.pstride + base, C::PROW,
+                     full + 8 * s);
+          }
         }
-        bulk_g2s(d, src, TILE_M * 4, full + 8 * s);
       }
     }
     if (!ok && lane == 0) atomicOr(a.err, 1);
@@ -433,6 +445,7 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
       if (*abort_flag) { ok = false; break; }
       const float* sA = reinterpret_cast<const float*>(stage0 + s * C::STAGE);
       const float* sP = sA + KP * TILE_M;
+      const __nv_bfloat16* sPh = reinterpret_cast<const __nv_bfloat16*>(sP);
       // 1. split this thread's point column of the staged snapshots
 #pragma unroll
       for (int k4 = 0; k4 < KP; k4 += 4) {
@@ -449,7 +462,15 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
       // 2. old accumulators of this point, then release the stage
       float pold[GRP];
 #pragma unroll
-      for (int i = 0; i < GRP; ++i) pold[i] = i < a.r ? sP[i * TILE_M + tid] : 0.f;
+      for (int i = 0; i < GRP; ++i) {
+        float v = 0.f;
+        if (i < a.r) {
+          if (ACC == 0) v = sP[i * TILE_M + tid];
+          else v = __bfloat162float(sPh[i * TILE_M + tid]);
+          if (ACC == 2) v += __bfloat162float(sPh[(GRP + i) * TILE_M + tid]);
+        }
+        pold[i] = v;
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + 8 * s);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -485,8 +506,20 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
           float acc[16];
           tmem_ld16(trow + (uint32_t)(c * 16), acc);
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c * 16 + j < a.r) P[(long long)(c * 16 + j) * a.pstride + prow] = pold[c * 16 + j] + acc[j];
+          for (int j = 0; j < 16; ++j) {
+            const int i = c * 16 + j;
+            if (i < a.r) {
+              const float nv = pold[i] + acc[j];
+              if (ACC == 0) {
+                Pf[(long long)i * a.pstride + prow] = nv;
+              } else {
+                const __nv_bfloat16 hv = __float2bfloat16_rn(nv);
+                Ph[(long long)i * a.pstride + prow] = hv;
+                // compensation: the rounding error of the stored value
+                if (ACC == 2) Ph[(long long)(a.r + i) * a.pstride + prow] = __float2bfloat16_rn(nv - __bfloat162float(hv));
+              }
+            }
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -500,13 +533,13 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
   }
 }
 
-template <int KP>
+template <int KP, int ACC>
 cudaError_t launch_tma(const GemmArgs& a, cudaStream_t s) {
-  using C = GCfg<KP>;
+  using C = GCfg<KP, ACC>;
   const int NP = std::max(16, (a.r + 15) / 16 * 16);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(probe_gemm_tma<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaFuncSetAttribute(probe_gemm_tma<KP, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     attr = true;
   }
   int dev = 0, sms = 1;
@@ -516,7 +549,7 @@ cudaError_t launch_tma(const GemmArgs& a, cudaStream_t s) {
   const long long ntiles = (long long)a.L.nz * a.L.ny * ((a.L.nx + TILE_M - 1) / TILE_M);
   const long long grid_x = std::min<long long>(ntiles, (long long)sms * occ);
   dim3 grid((unsigned)grid_x, a.nshots);
-  probe_gemm_tma<KP><<<grid, GTHREADS, C::SMEM, s>>>(a, NP, ntiles);
+  probe_gemm_tma<KP, ACC><<<grid, GTHREADS, C::SMEM, s>>>(a, NP, ntiles);
   return cudaGetLastError();
 }
 
@@ -559,8 +592,11 @@ cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
     return (e && strcmp(e, "regs") == 0) ? 1 : 0;
   }();
   cudaError_t e;
-  if (a.r <= GRP && variant == 0) {
-    e = a.nlev <= 32 ? launch_tma<32>(a, s) : launch_tma<64>(a, s);
+  if (a.acc != 0 || (a.r <= GRP && variant == 0)) {  // bf16 storage exists on this path only (r <= 32)
+    if (a.nlev <= 32)
+      e = a.acc == 0 ? launch_tma<32, 0>(a, s) : (a.acc == 1 ? launch_tma<32, 1>(a, s) : launch_tma<32, 2>(a, s));
+    else
+      e = a.acc == 0 ? launch_tma<64, 0>(a, s) : (a.acc == 1 ? launch_tma<64, 1>(a, s) : launch_tma<64, 2>(a, s));
   } else if (a.nlev <= 32) {
     e = a.r <= 16 ? launch_kp<32, 16>(a, s) : (a.r <= 32 ? launch_kp<32, 32>(a, s) : launch_kp<32, 0>(a, s));
   } else {

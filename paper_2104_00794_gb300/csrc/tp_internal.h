@@ -83,12 +83,16 @@ cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const St
 // The GEMM walks interior row segments of 128 points: M = nz * ny * nxt * 128
 // with nxt = ceil(nx / 128); padding columns beyond nx inside a segment are
 // zero in both operands and stay zero.
+// Accumulator storage: acc = 0 fp32; 1 bf16; 2 bf16 value + bf16 compensation
+// (the compensation of probe i is stored at element offset r * pstride after
+// its value).  P, pstride and p_ss count elements of the storage type.
 struct GemmArgs {
   Layout L;
   const float* ring; long long slot_stride; long long ring_ss; int nslots;
   int level0, nlev, qshift, qlo, qhi;
   const float* Q; int nt, r; long long q_ss;
-  float* P; long long pstride; long long p_ss;  // P[s][i] at P + s*p_ss + i*pstride
+  void* P; long long pstride; long long p_ss;  // P[s][i] at P + s*p_ss + i*pstride
+  int acc;
   int nshots;
   int q_has_lo;
   int* err;
@@ -133,6 +137,11 @@ cudaError_t launch_finalize_sum(const double* part, int nblk, double scale, doub
 // grad[x] = -scale_h2 * vel[x]^2 * sum_s gacc[s][off(x)]
 cudaError_t launch_finish_grad(const Layout& L, const float* vel, const float* gacc, int nshots,
                                long long gacc_ss, float scale_h2, float* grad, cudaStream_t s);
+// fp32 copy of accumulator field i of every shot: out[s] = value (+ compensation)
+cudaError_t launch_acc_to_f32(const void* P, int acc, int r, int i, long long field, int nshots, float* out,
+                              long long out_ss, cudaStream_t s);
+// grad <- grad * (-2 / vel^3): dJ/dv from dJ/dm (m = 1 / v^2)
+cudaError_t launch_chain_velocity(const float* vel, float* grad, long long n, cudaStream_t s);
 // qbar[s][k][i] = sum_{j=jlo}^{jhi} Q[s][j + qshift][i] * q[s][j][k]
 cudaError_t launch_qbar(const float* Q, int nt, int r, const float* wav, int nsrc, int nshots,
                         int jlo, int jhi, int qshift, float* qbar, cudaStream_t s);
@@ -140,7 +149,7 @@ cudaError_t launch_qbar(const float* Q, int nt, int r, const float* wav, int nsr
 // serial in a fixed order (deterministic when sources share a node)
 cudaError_t launch_source_term(const Layout& L, const float* vel, const int64_t* src_dense,
                                const long long* src_off, int nsrc, int nshots, float scale,
-                               const float* qbar, const float* V, int r, long long v_ss,
+                               const float* qbar, const void* V, int acc, int r, long long v_ss,
                                const double* srcacc, float* grad, cudaStream_t s);
 
 // message returned by tp_last_error() on the calling thread

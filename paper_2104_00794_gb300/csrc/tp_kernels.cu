@@ -1,4 +1,6 @@
 // Set-up, point-operator, probe-generation and reduction kernels.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "tp_internal.h"
@@ -179,9 +181,38 @@ __global__ void qbar_kernel(const float* __restrict__ Q, int nt, int r, const fl
   qbar[e] = (float)acc;
 }
 
+// value of accumulator i at element o of one shot's accumulator block
+__device__ __forceinline__ float acc_value(const void* P, int acc, int r, int i, long long field, long long o) {
+  if (acc == 0) return static_cast<const float*>(P)[(long long)i * field + o];
+  const __nv_bfloat16* h = static_cast<const __nv_bfloat16*>(P);
+  float v = __bfloat162float(h[(long long)i * field + o]);
+  if (acc == 2) v += __bfloat162float(h[(long long)(r + i) * field + o]);
+  return v;
+}
+
+__global__ void acc_to_f32_kernel(const void* __restrict__ P, int acc, int r, int i, long long field, int nshots,
+                                  float* __restrict__ out, long long out_ss) {
+  const long long per = acc == 2 ? 2LL * r * field : (long long)r * field;  // elements per shot
+  const long long n = (long long)nshots * field;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / field);
+    const long long o = e % field;
+    const void* Ps = acc == 0 ? (const void*)(static_cast<const float*>(P) + s * per)
+                              : (const void*)(static_cast<const __nv_bfloat16*>(P) + s * per);
+    out[s * out_ss + o] = acc_value(Ps, acc, r, i, field, o);
+  }
+}
+
+__global__ void chain_velocity_kernel(const float* __restrict__ vel, float* __restrict__ grad, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = vel[i];
+    grad[i] *= -2.0f / (v * v * v);
+  }
+}
+
 __global__ void source_term_kernel(Layout L, const float* __restrict__ vel, const int64_t* __restrict__ src,
                                    const long long* __restrict__ soff, int nsrc, int nshots, float scale,
-                                   const float* __restrict__ qbar, const float* __restrict__ V, int r,
+                                   const float* __restrict__ qbar, const void* __restrict__ V, int acc_mode, int r,
                                    long long v_ss, const double* __restrict__ srcacc, float* grad) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   const long long N = (long long)L.nx * L.ny * L.nz;
@@ -194,8 +225,10 @@ __global__ void source_term_kernel(Layout L, const float* __restrict__ vel, cons
       if (srcacc) {
         acc = srcacc[(long long)s * nsrc + k];
       } else {
+        const void* Vs = acc_mode == 0 ? (const void*)(static_cast<const float*>(V) + s * v_ss)
+                                       : (const void*)(static_cast<const __nv_bfloat16*>(V) + s * v_ss);
         for (int i = 0; i < r; ++i)
-          acc += (double)qbar[((long long)s * nsrc + k) * r + i] * (double)V[s * v_ss + (long long)i * L.field + o];
+          acc += (double)qbar[((long long)s * nsrc + k) * r + i] * (double)acc_value(Vs, acc_mode, r, i, L.field, o);
       }
       const float v = vel[p];
       grad[p] += (float)(-(double)scale * (double)v * (double)v * acc);
@@ -290,11 +323,26 @@ cudaError_t launch_qbar(const float* Q, int nt, int r, const float* wav, int nsr
 }
 
 cudaError_t launch_source_term(const Layout& L, const float* vel, const int64_t* src_dense, const long long* src_off,
-                               int nsrc, int nshots, float scale, const float* qbar, const float* V, int r,
+                               int nsrc, int nshots, float scale, const float* qbar, const void* V, int acc, int r,
                                long long v_ss, const double* srcacc, float* grad, cudaStream_t s) {
   prof_before(5, s);
-  source_term_kernel<<<1, 32, 0, s>>>(L, vel, src_dense, src_off, nsrc, nshots, scale, qbar, V, r, v_ss, srcacc,
+  source_term_kernel<<<1, 32, 0, s>>>(L, vel, src_dense, src_off, nsrc, nshots, scale, qbar, V, acc, r, v_ss, srcacc,
                                       grad);
+  prof_after(5, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_acc_to_f32(const void* P, int acc, int r, int i, long long field, int nshots, float* out,
+                              long long out_ss, cudaStream_t s) {
+  prof_before(5, s);
+  acc_to_f32_kernel<<<grid_for((long long)nshots * field, 256), 256, 0, s>>>(P, acc, r, i, field, nshots, out, out_ss);
+  prof_after(5, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain_velocity(const float* vel, float* grad, long long n, cudaStream_t s) {
+  prof_before(5, s);
+  chain_velocity_kernel<<<grid_for(n, 256), 256, 0, s>>>(vel, grad, n);
   prof_after(5, s);
   return cudaGetLastError();
 }

@@ -19,7 +19,8 @@ TP_OK, TP_ERR_ARG, TP_ERR_UNSTABLE, TP_ERR_NOMEM, TP_ERR_CUDA, TP_ERR_TIMEOUT = 
 STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_ARG", 2: "TP_ERR_UNSTABLE", 3: "TP_ERR_NOMEM", 4: "TP_ERR_CUDA",
                 5: "TP_ERR_TIMEOUT"}
 PROBE_KINDS = {"rademacher": 0, "gaussian": 1, "identity": 2, "user": 3}
-OP_FORWARD, OP_ADJOINT, OP_GRADIENT_PROBED, OP_GRADIENT_FULL = range(4)
+OP_FORWARD, OP_ADJOINT, OP_GRADIENT_PROBED, OP_GRADIENT_FULL, OP_PROBED_FORWARD, OP_PROBED_BACKWARD = range(6)
+ACC_TYPES = {"f32": 0, "bf16": 1, "bf16_kahan": 2}
 KERNEL_KINDS = 6
 
 
@@ -36,7 +37,7 @@ class tp_geom(ctypes.Structure):
 
 class tp_probe(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("r", ctypes.c_int), ("T", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("Z_user", ctypes.c_void_p), ("scale", ctypes.c_float)]
+                ("Z_user", ctypes.c_void_p), ("scale", ctypes.c_float), ("acc", ctypes.c_int)]
 
 
 class TprobeError(RuntimeError):
@@ -68,13 +69,18 @@ def lib():
         L.tp_probes.argtypes = [Pr, i32, i32, vp, vp]
         L.tp_workspace_status.argtypes = [vp, sz, vp]
         L.tp_misfit_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+        L.tp_probed_state_bytes.argtypes = [G, E, Pr]
+        L.tp_probed_state_bytes.restype = sz
+        L.tp_probed_forward.argtypes = [G, E, Pr, vp, vp, vp, vp, sz, vp, sz, vp]
+        L.tp_probed_backward.argtypes = [G, E, Pr, vp, vp, vp, i32, vp, vp, vp, sz, vp, sz, vp]
         L.tp_last_error.restype = ctypes.c_char_p
         L.tp_profile_begin.argtypes = [i32]
         L.tp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         L.tp_kernel_name.argtypes = [i32]
         L.tp_kernel_name.restype = ctypes.c_char_p
         for f in ("tp_forward", "tp_adjoint", "tp_gradient_probed", "tp_gradient_full", "tp_probes",
-                  "tp_workspace_status", "tp_profile_begin", "tp_profile_end", "tp_misfit_noalloc"):
+                  "tp_workspace_status", "tp_profile_begin", "tp_profile_end", "tp_misfit_noalloc",
+                  "tp_probed_forward", "tp_probed_backward"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
         return L
@@ -114,6 +120,25 @@ def tp_gradient_probed(grid, geom, probe, vel, wavelet, d_obs, grad, misfit, gno
 def tp_gradient_full(grid, geom, vel, wavelet, d_obs, grad, misfit, gnorm, ws, ws_bytes, stream):
     _check(lib().tp_gradient_full(ctypes.byref(grid), ctypes.byref(geom), vel, wavelet, d_obs, grad, misfit,
                                   gnorm, ws, ws_bytes, stream))
+
+
+def tp_probed_state_bytes(grid, geom, probe) -> int:
+    n = lib().tp_probed_state_bytes(ctypes.byref(grid), ctypes.byref(geom), ctypes.byref(probe))
+    if n == 0:
+        raise TprobeError(TP_ERR_ARG, last_error())
+    return int(n)
+
+
+def tp_probed_forward(grid, geom, probe, vel, wavelet, d_out, state, state_bytes, ws, ws_bytes, stream):
+    _check(lib().tp_probed_forward(ctypes.byref(grid), ctypes.byref(geom), ctypes.byref(probe), vel, wavelet, d_out,
+                                   state, state_bytes, ws, ws_bytes, stream))
+
+
+def tp_probed_backward(grid, geom, probe, vel, wavelet, adj_src, wrt_velocity, grad, gnorm, state, state_bytes, ws,
+                       ws_bytes, stream):
+    _check(lib().tp_probed_backward(ctypes.byref(grid), ctypes.byref(geom), ctypes.byref(probe), vel, wavelet,
+                                    adj_src, int(wrt_velocity), grad, gnorm, state, state_bytes, ws, ws_bytes,
+                                    stream))
 
 
 def tp_probes(probe, nt, shot, Z, stream):
