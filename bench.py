@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--no-full", action="store_true", help="skip the full-storage comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-nt", type=int, default=16, help="time levels of the bounded CPU sample")
+    ap.add_argument("--cpu-nt", type=int, default=48, help="time levels of the bounded CPU sample")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving (p50/p99) leg")
+    ap.add_argument("--serve-requests", type=int, default=16)
     return ap.parse_args()
 
 
@@ -165,6 +167,67 @@ def run_reference(args, rank: int):
         "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ serving leg
+def serving_mix(n: int, seed: int):
+    """Request mix: 2-D grids 201^2 .. 1001x401 and 3-D 128^3 .. 320^3, nt in
+    [1000, 4000], r in {8, 16, 32}, order 8, probed gradients (one shot)."""
+    from paper_2104_00794_gb300 import workloads as wl
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nt = int(rng.integers(1000, 4001))
+        r = int(rng.choice([8, 16, 32]))
+        if rng.uniform() < 0.5:
+            nx = int(rng.integers(201, 1002))
+            nz = int(rng.integers(201, min(nx, 401) + 1))
+            w = wl.small_2d(nx=nx, nz=nz, nt=nt, order=8, r=r, probe_kind="rademacher", h=10.0, dt=1e-3,
+                            f0=10.0, seed=seed + i)
+        else:
+            m = int(rng.integers(128, 321))
+            w = wl.config3(n=m, nt=nt, r=r, seed=seed + i, rec_stride=2)
+        out.append(w)
+    return out
+
+
+def run_serving(args, rank):
+    import torch
+    from paper_2104_00794_gb300 import api, serve
+    mix = serving_mix(args.serve_requests, seed=wl_seed() + 17 * rank)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    jobs = []
+    for w in mix:
+        p = api.Problem.from_workload(w)
+        dobs = p.forward(dev(w.vel_true), dev(w.wavelet)).clone()
+        p.release()
+        jobs.append(serve.GradientJob(p, dev(w.vel0), dev(w.wavelet), dobs,
+                                      api.ProbeSpec(kind="rademacher", r=w.r, T=32, seed=w.seed)))
+    torch.cuda.synchronize()
+    work = [2.0 * w.N * w.nt for w in mix]
+    # service-time estimate from the 3-D rate, arrival rate for ~75 % busy
+    est = float(np.mean(work)) / 150e9
+    rng = np.random.default_rng(99 + rank)
+    arrivals = np.cumsum(rng.exponential(est / 0.75, size=len(mix)))
+    arrivals -= arrivals[0]
+    reqs = [serve.Request(i, float(arrivals[i]), jobs[i].footprint(), work[i], jobs[i]) for i in range(len(mix))]
+    budget = int(80e9)
+    sched = serve.Scheduler(budget, max_slots=6)
+    ex = serve.GpuExecutor(use_graphs=True)
+    t0 = time.perf_counter()
+    serve.run(reqs, sched, ex.start, ex.poll)
+    torch.cuda.synchronize()
+    makespan = time.perf_counter() - t0
+    s = serve.summarize(reqs, makespan)
+    s.update({"slots_max": sched.max_slots, "peak_concurrent": sched.peak_active, "budget_bytes": budget,
+              "peak_bytes": sched.peak_used, "mix": "2-D 201^2..1001x401 and 3-D 128^3..320^3, nt 1000-4000, r 8/16/32",
+              "arrivals": "Poisson, rate for ~75 % busy", "graphs": True})
+    return s
+
+
+def wl_seed():
+    from paper_2104_00794_gb300 import workloads as wl
+    return wl.DEFAULT_SEED
 
 
 # ------------------------------------------------------------------ our arm
@@ -317,6 +380,11 @@ def main():
                "seconds": tc}
         pc.release()
 
+    # ---- serving: Poisson stream of mixed-size shot-gradient requests
+    serving = None
+    if not args.no_serve:
+        serving = run_serving(args, rank)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
@@ -341,6 +409,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "err_vs_fp64": err,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

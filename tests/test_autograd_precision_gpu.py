@@ -61,7 +61,7 @@ def test_autograd_identity_probes_match_oracle_gradient():
     # J = |res|^2 / 2: a trace error of 1e-5 |d| moves J by at most 2e-5 |d| / |res| relative
     res_ref = oracle.batch_forward(w, w.vel0) - dobs_np
     tol_j = 2e-5 * np.linalg.norm(dobs_np) / np.linalg.norm(res_ref)
-    assert float(loss) == pytest.approx(J, rel=tol_j)
+    assert float(loss.detach()) == pytest.approx(J, rel=tol_j)
     assert rel_l2(gv, gv_ref) <= 1e-4
 
 
