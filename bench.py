@@ -41,10 +41,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config3", choices=["config1", "config2", "config3", "config4"],
+                    help="config3 (3-D 256^3) is the headline; the 2-D configs are L2-resident")
     ap.add_argument("--n", type=int, default=256, help="grid points per axis")
     ap.add_argument("--nt", type=int, default=2000)
     ap.add_argument("--r", type=int, default=32)
     ap.add_argument("--T", type=int, default=32)
+    ap.add_argument("--form", default="levels", choices=["levels", "increment"], help="fp32 time-stepping form")
     ap.add_argument("--no-full", action="store_true", help="skip the full-storage comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -136,6 +139,36 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ workloads
+def make_workload(args, nt=None, seed_offset=0):
+    from paper_2104_00794_gb300 import workloads as wl
+    seed = wl.DEFAULT_SEED + seed_offset
+    if args.workload == "config3":
+        return wl.config3(n=args.n, nt=nt or args.nt, T=args.T, r=args.r, seed=seed)
+    w = {"config1": wl.config1, "config2": wl.config2, "config4": wl.config4}[args.workload](seed=seed)
+    if nt:
+        w = truncate(w, nt)
+    return w
+
+
+def truncate(w, nt):
+    import dataclasses
+    return dataclasses.replace(w, nt=nt, wavelet=np.ascontiguousarray(w.wavelet[:, :nt]), name=w.name + f"_nt{nt}")
+
+
+def cpu_sample(args):
+    """A bounded sample of the workload for the FP64 oracle (10-30 s of CPU)."""
+    w = make_workload(args)
+    if args.workload == "config3":
+        return make_workload(args, nt=args.cpu_nt), f"256^3 grid, nt={args.cpu_nt} of {w.nt} levels, r={w.r}"
+    import dataclasses
+    shots = 1 if args.workload != "config1" else w.nshots
+    ws = dataclasses.replace(w, nshots=shots, src=w.src[:shots], rec=w.rec[:shots], wavelet=w.wavelet[:shots])
+    if args.workload != "config1":
+        ws = truncate(ws, min(w.nt, 1500))
+    return ws, f"{shots} of {w.nshots} shots, nt={ws.nt} of {w.nt}, r={w.r}"
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank: int):
     """The FP64 CPU oracle on a bounded sample of the same workload."""
@@ -143,8 +176,8 @@ def run_reference(args, rank: int):
         return
     import oracle
     from paper_2104_00794_gb300 import workloads as wl
-    w = wl.config3(n=args.n, nt=args.cpu_nt, T=args.T, r=args.r)
-    dobs = wl.synthetic_data(1, w.nt, w.nrec, seed=7)
+    w, sample = cpu_sample(args)
+    dobs = wl.synthetic_data(w.nshots, w.nt, w.nrec, seed=7)
     oracle.build()
     times = []
     for i in range(args.warmup + args.steps):
@@ -154,16 +187,15 @@ def run_reference(args, rank: int):
         if i >= args.warmup:
             times.append(dt)
     t = statistics.median(times)
-    v = 2.0 * w.N * w.nt / t / 1e9
+    v = 2.0 * w.N * w.nt * w.nshots / t / 1e9
     cores = os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Gpts/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "sample": f"probed gradient, nt cut to {w.nt} of 2000 levels",
+        "config": {"workload": make_workload(args).name, "sample": f"probed gradient, {sample}",
                    "grid": [w.nz, w.ny, w.nx], "r": w.r},
-        "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
-                         "sample": f"256^3 grid, nt={w.nt} (both passes), r={w.r}"},
+        "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -260,12 +292,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    w = wl.config3(n=args.n, nt=args.nt, T=args.T, r=args.r, seed=wl.DEFAULT_SEED + rank)
-    p = api.Problem.from_workload(w)
+    w = make_workload(args, seed_offset=rank)
+    p = api.Problem.from_workload(w, form=args.form)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     vel_true, vel0, wav = dev(w.vel_true), dev(w.vel0), dev(w.wavelet)
     d_obs = p.forward(vel_true, wav).clone()  # observed data of the true model (setup, untimed)
-    probe = api.ProbeSpec(kind="rademacher", r=w.r, T=w.T, seed=w.seed)
+    probe = api.ProbeSpec(kind=w.probe_kind, r=w.r, T=w.T, seed=w.seed)
     grad = torch.empty(p.shape, dtype=torch.float32, device="cuda")
     scal = torch.empty(2, dtype=torch.float64, device="cuda")
     pts = 2.0 * w.N * w.nt * w.nshots  # grid-point updates per gradient (fwd + adj)
@@ -311,7 +343,7 @@ def main():
     from paper_2104_00794_gb300.native import tp_probe  # noqa: F401
     # the GEMM walks interior row segments of 128 points: T snapshots read,
     # r accumulators read and written per point
-    gemm_pts = w.nz * w.ny * ((w.nx + 127) // 128 * 128)
+    gemm_pts = w.nz * w.ny * ((w.nx + 127) // 128 * 128) * w.nshots
     gemm_bytes = gemm_pts * 4 * (w.T + 2 * w.r)
     gemm_flops = 2.0 * gemm_pts * w.T * w.r * 2  # hi and lo products (Rademacher probes exact in tf32)
     launches = sum(v["launches"] for v in kern.values())
@@ -362,27 +394,26 @@ def main():
     err = None
     if not args.no_cpu and rank == 0 and world == 1:
         import oracle
-        wc = wl.config3(n=args.n, nt=args.cpu_nt, T=args.T, r=args.r, seed=wl.DEFAULT_SEED)
+        wc, sample = cpu_sample(args)
         pc = api.Problem.from_workload(wc)
-        dobs_c = wl.synthetic_data(1, wc.nt, wc.nrec, seed=7)
+        dobs_c = wl.synthetic_data(wc.nshots, wc.nt, wc.nrec, seed=7)
         oracle.build()
         t0 = time.perf_counter()
         gref, Jref = oracle.batch_gradient_probed(wc, wc.vel0, dobs_c)
         tc = time.perf_counter() - t0
         gcpu, sc = pc.gradient_probed(dev(wc.vel0), dev(wc.wavelet), dev(dobs_c),
-                                      api.ProbeSpec(kind="rademacher", r=wc.r, T=wc.T, seed=wc.seed))
+                                      api.ProbeSpec(kind=wc.probe_kind, r=wc.r, T=wc.T, seed=wc.seed))
         gg = gcpu.double().cpu().numpy().ravel()
         err = {"probed_gradient_rel_l2": float(np.linalg.norm(gg - gref) / np.linalg.norm(gref)),
                "misfit_rel": abs(float(sc[0].item()) - Jref) / Jref,
-               "case": f"256^3, nt={wc.nt}, r={wc.r}, same probes"}
-        cpu = {"value": 2.0 * wc.N * wc.nt / tc / 1e9, "unit": "Gpts/s", "cores": os.cpu_count(),
-               "kind": "oracle", "sample": f"probed gradient on the 256^3 grid with nt={wc.nt} (of 2000), r={wc.r}",
-               "seconds": tc}
+               "case": f"{sample}, same probes"}
+        cpu = {"value": 2.0 * wc.N * wc.nt * wc.nshots / tc / 1e9, "unit": "Gpts/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"probed gradient, {sample}", "seconds": tc}
         pc.release()
 
     # ---- serving: Poisson stream of mixed-size shot-gradient requests
     serving = None
-    if not args.no_serve:
+    if not args.no_serve and args.workload == "config3":
         serving = run_serving(args, rank)
 
     if rank == 0:
@@ -392,7 +423,9 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "grid": [w.nz, w.ny, w.nx], "h_m": w.h, "nt": w.nt, "dt_s": w.dt,
                        "order": w.order, "shots_per_gpu": w.nshots, "nrec": w.nrec, "r": w.r, "T": w.T,
-                       "probes": "rademacher", "l2": "inputs larger than L2 (fields 67 MB, >100 GB streamed per step)",
+                       "probes": w.probe_kind,
+                       "l2": ("inputs larger than L2 (fields 67 MB, >100 GB streamed per step)" if w.ndim == 3 else
+                              "2-D batch is L2-resident (no flush): reported for completeness, not an HBM roofline"),
                        "parallelism": f"replicas x{world}"},
             "roofline": {"kernel": "stencil_step", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_kind,

@@ -88,7 +88,14 @@ typedef struct {
   float vmax;  /* > 0: caller-asserted max velocity used for the CFL check
                   (no device synchronisation); 0: the library reduces the
                   velocity on the device and synchronises the stream once */
+  int form;    /* fp32 time stepping of the same scheme: TP_FORM_LEVELS keeps
+                  (u[t], u[t-1]); TP_FORM_INCREMENT keeps (u[t], u[t] - u[t-1]),
+                  so that the rounding of u is integrated once instead of
+                  twice (more accurate over thousands of steps, one more
+                  4-byte write per point and step) */
 } tp_grid;
+
+typedef enum { TP_FORM_LEVELS = 0, TP_FORM_INCREMENT = 1 } tp_form;
 
 /* Acquisition of a batch of independent shots sharing one model.  S^T and R
  * of Eq. 2 / Algorithm 1: on-grid point sources and receivers. */

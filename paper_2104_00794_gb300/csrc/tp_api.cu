@@ -119,11 +119,11 @@ struct Plan {
   int op = 0;
   Layout L{};
   Weights W{};
-  int nshots = 0, nsrc = 0, nrec = 0, nt = 0, r = 0, T = 0, S = 0, kind = 0, acc = 0;
+  int nshots = 0, nsrc = 0, nrec = 0, nt = 0, r = 0, T = 0, S = 0, kind = 0, acc = 0, form = 0;
   float scale = 1.f;
   size_t bytes = 0;
   size_t o_scal = 0, o_part = 0, o_c2 = 0, o_f = 0, o_P = 0, o_V = 0, o_Q = 0, o_d = 0, o_soff = 0, o_roff = 0,
-         o_cs = 0, o_cr = 0, o_qbar = 0, o_gacc = 0, o_sacc = 0, o_conv = 0;
+         o_cs = 0, o_cr = 0, o_qbar = 0, o_gacc = 0, o_sacc = 0, o_conv = 0, o_w = 0;
   long long nf = 0;  // fields in the wavefield block
   // probed state (Q, then the forward accumulators): offsets inside the state
   // buffer, which tp_gradient_probed places at o_state of its workspace
@@ -149,6 +149,7 @@ tp_status check_grid(const tp_grid* g) {
   if ((long long)g->nx * g->ny * g->nz > (1LL << 40)) return fail(TP_ERR_ARG, "grid too large");
   if (g->nx > (1 << 24) || g->nz > (1 << 24) || g->ny > (1 << 24)) return fail(TP_ERR_ARG, "grid extent too large");
   if (!(g->vmax >= 0.f)) return fail(TP_ERR_ARG, "vmax must be >= 0");
+  if (g->form != TP_FORM_LEVELS && g->form != TP_FORM_INCREMENT) return fail(TP_ERR_ARG, "unknown time form %d", g->form);
   return TP_OK;
 }
 
@@ -198,6 +199,8 @@ tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe
   P->o_cs = take(cur, (size_t)ns * P->nsrc * sizeof(float));
   P->o_cr = take(cur, (size_t)ns * P->nrec * sizeof(float));
   P->o_c2 = take(cur, fb);
+  P->form = g->form;
+  if (P->form == TP_FORM_INCREMENT) P->o_w = take(cur, (size_t)ns * fb);  // the increment field of each shot
   switch (op) {
     case TP_OP_FORWARD:
     case TP_OP_ADJOINT:
@@ -290,8 +293,8 @@ tp_status setup(const Ctx& c, const tp_grid* g, const tp_geom* geo, const float*
   if (!vel) return fail(TP_ERR_ARG, "vel is NULL");
   TRY(cudaMemsetAsync(c.scal(), 0, SCAL_BYTES, c.st));
   TRY(cudaMemsetAsync(c.at<float>(P.o_c2), 0, (size_t)P.L.field * sizeof(float), c.st));
-  const float dt2 = g->dt * g->dt;
-  TRY(launch_prep_c2(P.L, vel, dt2 / (g->h * g->h), c.at<float>(P.o_c2), c.st));
+  const double dt2 = (double)g->dt * (double)g->dt;
+  TRY(launch_prep_c2(P.L, vel, dt2 / ((double)g->h * (double)g->h), c.at<float>(P.o_c2), c.st));
   TRY(launch_prep_points(P.L, geo->src, (long long)P.nshots * P.nsrc, vel, dt2, c.at<long long>(P.o_soff),
                          c.at<float>(P.o_cs), c.err(), c.st));
   TRY(launch_prep_points(P.L, geo->rec, (long long)P.nshots * P.nrec, vel, dt2, c.at<long long>(P.o_roff),
@@ -312,9 +315,19 @@ tp_status setup(const Ctx& c, const tp_grid* g, const tp_geom* geo, const float*
   return TP_OK;
 }
 
+// the increment fields (TP_FORM_INCREMENT), one per shot
+Fam inc_fam(const Plan& P) { return Fam{P.o_w, P.nshots, 1}; }
+
 tp_status step(const Ctx& c, const Fam& f, int cur, int old, int out) {
-  StencilArgs a{c.ref(f, cur), c.ref(f, old), c.ref(Fam{c.P.o_c2, 1, 0}, 0), c.ptr(f, out), c.ss(f), c.P.nshots};
-  TRY(launch_stencil(MODE_STEP, c.P.L, c.P.W, a, c.st, c.err()));
+  const FieldRef c2 = c.ref(Fam{c.P.o_c2, 1, 0}, 0);
+  if (c.P.form == TP_FORM_INCREMENT) {
+    const Fam fw = inc_fam(c.P);
+    StencilArgs a{c.ref(f, cur), c.ref(fw, 0), c2, c.ptr(f, out), c.ss(f), c.P.nshots, c.ptr(fw, 0), c.ss(fw)};
+    TRY(launch_stencil(MODE_INC, c.P.L, c.P.W, a, c.st, c.err()));
+  } else {
+    StencilArgs a{c.ref(f, cur), c.ref(f, old), c2, c.ptr(f, out), c.ss(f), c.P.nshots};
+    TRY(launch_stencil(MODE_STEP, c.P.L, c.P.W, a, c.st, c.err()));
+  }
   return TP_OK;
 }
 
@@ -328,6 +341,10 @@ tp_status point(const Ctx& c, const float* samp, long long samp_ss, const long l
   a.field_samp = samp; a.samp_ss = samp_ss; a.samp_off = soff; a.nsamp = samp ? nsamp : 0;
   a.samp_out = out; a.samp_out_ss = out_ss;
   a.field_inj = inj; a.inj_ss = inj_ss; a.inj_off = ioff; a.inj_coef = icoef; a.ninj = inj ? ninj : 0;
+  if (inj && c.P.form == TP_FORM_INCREMENT) {  // sources enter the increment as well as the new level
+    a.field_inj2 = c.ptr(inc_fam(c.P), 0);
+    a.inj2_ss = c.ss(inc_fam(c.P));
+  }
   a.inj_val = ival; a.inj_val_ss = ival_ss;
   a.acc = acc; a.acc_val = aval; a.acc_val_ss = aval_ss;
   TRY(launch_point(a, c.st));
@@ -347,6 +364,8 @@ template <class LevelFn, class AfterFn>
 tp_status forward_loop(const Ctx& c, const Fam& f, LevelFn level, const float* wav, float* d, AfterFn after_level) {
   const Plan& P = c.P;
   const long long dss = (long long)P.nt * P.nrec, wss = (long long)P.nt * P.nsrc, ss = c.ss(f);
+  if (P.form == TP_FORM_INCREMENT)  // u[1] - u[0] = 0
+    TRY(cudaMemsetAsync(c.at<char>(P.o_w), 0, (size_t)P.nshots * P.L.field * sizeof(float), c.st));
   for (int t = 1; t <= P.nt - 2; ++t) {
     TRYS(step(c, f, level(t), level(t - 1), level(t + 1)));
     TRYS(point(c, d ? c.ptr(f, level(t)) : nullptr, ss, c.at<long long>(P.o_roff), P.nrec,
@@ -369,6 +388,8 @@ tp_status adjoint_loop(const Ctx& c, const Fam& f, LevelFn level, const float* s
   const Plan& P = c.P;
   const long long sss = (long long)P.nt * P.nrec, qss = (long long)P.nt * P.nsrc, ss = c.ss(f);
   const bool samp = q_out || acc;
+  if (P.form == TP_FORM_INCREMENT)  // lambda[nt] - lambda[nt+1] = 0
+    TRY(cudaMemsetAsync(c.at<char>(P.o_w), 0, (size_t)P.nshots * P.L.field * sizeof(float), c.st));
   for (int j = P.nt - 1; j >= 2; --j) {
     TRYS(step(c, f, level(j + 1), level(j + 2), level(j)));
     TRYS(point(c, samp ? c.ptr(f, level(j + 1)) : nullptr, ss, c.at<long long>(P.o_soff), P.nsrc,

@@ -41,6 +41,9 @@ struct Layout {
 Layout make_layout(int ndim, int nx, int ny, int nz);
 
 // Centred second-derivative weights w[0..R] (Fornberg 1988) for order 2R.
+// The sweeps use w[1..R] in the difference form sum_k w_k (u[+k] + u[-k] - 2u)
+// per axis, which equals w[0] u + sum_k w_k (u[+k] + u[-k]) because
+// w[0] = -2 sum_k w_k, and stays exact for constants in fp32.
 struct Weights {
   float w[5];
   int R;
@@ -48,7 +51,7 @@ struct Weights {
 Weights stencil_weights(int order);
 
 // ---------------------------------------------------------------- stencil
-enum StencilMode { MODE_STEP = 0, MODE_IMAGE = 1 };
+enum StencilMode { MODE_STEP = 0, MODE_IMAGE = 1, MODE_INC = 2 };
 
 // A field of a "family": `nfields` consecutive padded fields starting at
 // `base` (a ring of levels, a history, the accumulators...).  Shot s uses
@@ -64,14 +67,18 @@ struct FieldRef {
 };
 
 // MODE_STEP : out = 2 src - p1 + p2 * S(src)          (leapfrog, p1 = older level, p2 = c2)
+// MODE_INC  : w' = p1 + p2 * S(src), out = src + w', and w' is stored to out2
+//             (the increment form: p1 = out2 = the increment u[t] - u[t-1])
 // MODE_IMAGE: out = p2 + p1 * S(src)  (out may alias p2: accumulate)
-// S(.) = sum of stencil weights (no 1/h^2).  `out` is the shot-0 field,
+// S(.) = the stencil sum without 1/h^2, in the difference form.  `out` is the shot-0 field,
 // out_ss the per-shot stride in floats.
 struct StencilArgs {
   FieldRef src, p1, p2;
   float* out;
   long long out_ss;
   int nshots;
+  float* out2 = nullptr;     // MODE_INC: the increment field (same storage as p1)
+  long long out2_ss = 0;
 };
 cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& a,
                            cudaStream_t s, int* err);
@@ -101,12 +108,12 @@ cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s);
 int gemm_kpad(int T);
 
 // ---------------------------------------------------------------- misc kernels
-cudaError_t launch_prep_c2(const Layout& L, const float* vel, float coef, float* c2, cudaStream_t s);
+cudaError_t launch_prep_c2(const Layout& L, const float* vel, double coef, float* c2, cudaStream_t s);
 cudaError_t launch_vmax(const float* vel, long long n, unsigned int* out_bits, cudaStream_t s);
 // dense node indices -> padded offsets, and injection coefficient dt^2 v^2 at each point
 // (out-of-range indices get offset -1 and set bit 2 of *err)
 cudaError_t launch_prep_points(const Layout& L, const int64_t* idx, long long n, const float* vel,
-                               float dt2, long long* off, float* cinj, int* err, cudaStream_t s);
+                               double dt2, long long* off, float* cinj, int* err, cudaStream_t s);
 
 // One thread per point of two independent sets, all shots:
 //   sample: samp_out[s][t_s][j] = field_samp[s][samp_off[s][j]]           (j < nsamp)
@@ -117,6 +124,7 @@ struct PointArgs {
   const float* field_samp; long long samp_ss;
   const long long* samp_off; int nsamp; float* samp_out; long long samp_out_ss;  // already offset to t
   float* field_inj; long long inj_ss;
+  float* field_inj2; long long inj2_ss;  // optional second target (the increment field)
   const long long* inj_off; const float* inj_coef; int ninj;
   const float* inj_val; long long inj_val_ss;  // already offset to t
   double* acc; const float* acc_val; long long acc_val_ss;  // may be null

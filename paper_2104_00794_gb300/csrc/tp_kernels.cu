@@ -11,11 +11,14 @@ namespace {
 
 constexpr int RED_THREADS = 256;
 
-__global__ void prep_c2_kernel(Layout L, const float* __restrict__ vel, float coef, float* __restrict__ c2) {
+// c2 = dt^2 v^2 / h^2 formed in fp64 and rounded once: an fp32 product chain
+// is off by a few ulp, i.e. a velocity error of ~1e-7 whose phase error grows
+// linearly with time (the dominant fp32 trace error after thousands of steps).
+__global__ void prep_c2_kernel(Layout L, const float* __restrict__ vel, double coef, float* __restrict__ c2) {
   const long long n = (long long)L.nx * L.ny * L.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float v = vel[i];
-    c2[L.off_flat(i)] = coef * v * v;
+    const double v = vel[i];
+    c2[L.off_flat(i)] = (float)(coef * v * v);
   }
 }
 
@@ -28,7 +31,7 @@ __global__ void vmax_kernel(const float* __restrict__ vel, long long n, unsigned
 }
 
 __global__ void prep_points_kernel(Layout L, const int64_t* __restrict__ idx, long long n,
-                                   const float* __restrict__ vel, float dt2, long long* __restrict__ off,
+                                   const float* __restrict__ vel, double dt2, long long* __restrict__ off,
                                    float* __restrict__ cinj, int* err) {
   const long long N = (long long)L.nx * L.ny * L.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -39,8 +42,8 @@ __global__ void prep_points_kernel(Layout L, const int64_t* __restrict__ idx, lo
       atomicOr(err, 2);
     } else {
       off[i] = L.off_flat(p);
-      const float v = vel[p];
-      cinj[i] = dt2 * v * v;
+      const double v = vel[p];
+      cinj[i] = (float)(dt2 * v * v);
     }
   }
 }
@@ -60,7 +63,11 @@ __global__ void point_kernel(PointArgs a) {
   if (k2 < (long long)a.nshots * a.ninj) {
     const int s = (int)(k2 / a.ninj), k = (int)(k2 % a.ninj);
     const long long o = a.inj_off[k2];
-    if (o >= 0) atomicAdd(a.field_inj + s * a.inj_ss + o, a.inj_coef[k2] * a.inj_val[s * a.inj_val_ss + k]);
+    if (o >= 0) {
+      const float v = a.inj_coef[k2] * a.inj_val[s * a.inj_val_ss + k];
+      atomicAdd(a.field_inj + s * a.inj_ss + o, v);
+      if (a.field_inj2) atomicAdd(a.field_inj2 + s * a.inj2_ss + o, v);
+    }
   }
 }
 
@@ -241,7 +248,7 @@ int grid_for(long long n, int threads, int cap = 8192) {
 
 }  // namespace
 
-cudaError_t launch_prep_c2(const Layout& L, const float* vel, float coef, float* c2, cudaStream_t s) {
+cudaError_t launch_prep_c2(const Layout& L, const float* vel, double coef, float* c2, cudaStream_t s) {
   prof_before(5, s);
   const long long n = (long long)L.nx * L.ny * L.nz;
   prep_c2_kernel<<<grid_for(n, 256), 256, 0, s>>>(L, vel, coef, c2);
@@ -256,7 +263,7 @@ cudaError_t launch_vmax(const float* vel, long long n, unsigned int* out, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_points(const Layout& L, const int64_t* idx, long long n, const float* vel, float dt2,
+cudaError_t launch_prep_points(const Layout& L, const int64_t* idx, long long n, const float* vel, double dt2,
                                long long* off, float* cinj, int* err, cudaStream_t s) {
   prof_before(5, s);
   prep_points_kernel<<<grid_for(n, 256), 256, 0, s>>>(L, idx, n, vel, dt2, off, cinj, err);

@@ -28,15 +28,21 @@ struct PlainArgs {
   const float* p2;   long long p2_ss;
   float* out;        long long out_ss;
   int nshots;
+  float* out2;       long long out2_ss;  // MODE_INC: increment field
 };
 
 __device__ __forceinline__ float4 ld4(const float* base, long long idx) {
   return __ldg(reinterpret_cast<const float4*>(base + idx));
 }
 
+// returns the new value; in MODE_INC also the new increment through *inc
 template <int MODE>
-__device__ __forceinline__ float epilogue(float c, float s, float p1, float p2) {
+__device__ __forceinline__ float epilogue(float c, float s, float p1, float p2, float* inc) {
   if (MODE == MODE_STEP) return fmaf(p2, s, 2.0f * c - p1);
+  if (MODE == MODE_INC) {
+    *inc = fmaf(p2, s, p1);
+    return c + *inc;
+  }
   return fmaf(p1, s, p2);
 }
 
@@ -97,7 +103,6 @@ sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
   if (hxl) nhx = ld4(src, colxl + (long long)zb * pl);
   if (hxr) nhx = ld4(src, colxr + (long long)zb * pl);
 
-  const float w0 = 3.0f * W.w[0];
   for (int z = zb; z < ze; ++z) {
     q[2 * R] = nq;
     // stage plane z (centre from the queue, halo from the prefetch registers)
@@ -125,24 +130,26 @@ sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
 
     const float4 xl = sm[ty + R][tx], xc = sm[ty + R][tx + 1], xr = sm[ty + R][tx + 2];
     const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-    float s[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) s[p] = w0 * v[4 + p];
+    float s[4] = {0.f, 0.f, 0.f, 0.f};  // difference form (see tp_sweep3d_tma.cu)
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
       const float4 yp = sm[ty + R + k][tx + 1], ym = sm[ty + R - k][tx + 1];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const float t = (v[4 + p + k] + v[4 + p - k]) + (comp(yp, p) + comp(ym, p)) +
-                        (comp(q[R + k], p) + comp(q[R - k], p));
+        const float c = v[4 + p];
+        const float t = ((v[4 + p + k] - c) + (v[4 + p - k] - c)) + ((comp(yp, p) - c) + (comp(ym, p) - c)) +
+                        ((comp(q[R + k], p) - c) + (comp(q[R - k], p) - c));
         s[p] = fmaf(W.w[k], t, s[p]);
       }
     }
-    float res[4];
+    float res[4], inc[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) res[p] = epilogue<MODE>(v[4 + p], s[p], comp(c1, p), comp(c2, p));
-    if (y < L.ny && x < L.nx)
+    for (int p = 0; p < 4; ++p) res[p] = epilogue<MODE>(v[4 + p], s[p], comp(c1, p), comp(c2, p), &inc[p]);
+    if (y < L.ny && x < L.nx) {
       store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
+      if (MODE == MODE_INC)
+        store_masked(a.out2 + shot * a.out2_ss, colc + (long long)z * pl, make_float4(inc[0], inc[1], inc[2], inc[3]), x, L.nx);
+    }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
@@ -186,7 +193,6 @@ sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) 
   if (hxl) nhx = ld4(src, colxl + (long long)zb * pl);
   if (hxr) nhx = ld4(src, colxr + (long long)zb * pl);
 
-  const float w0 = 2.0f * W.w[0];
   for (int z = zb; z < ze; ++z) {
     q[2 * R] = nq;
     sm[wi][lane + 1] = q[R];
@@ -204,19 +210,23 @@ sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) 
     __syncwarp();
     const float4 xl = sm[wi][lane], xc = sm[wi][lane + 1], xr = sm[wi][lane + 2];
     const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-    float res[4];
+    float res[4], inc[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       const float c = v[4 + p];
-      float s = w0 * c;
+      float s = 0.f;  // difference form: annihilates constants whatever the weight rounding
 #pragma unroll
       for (int k = 1; k <= R; ++k) {
-        const float t = (v[4 + p + k] + v[4 + p - k]) + (comp(q[R + k], p) + comp(q[R - k], p));
+        const float t = ((v[4 + p + k] - c) + (v[4 + p - k] - c)) + ((comp(q[R + k], p) - c) + (comp(q[R - k], p) - c));
         s = fmaf(W.w[k], t, s);
       }
-      res[p] = epilogue<MODE>(c, s, comp(c1, p), comp(c2, p));
+      res[p] = epilogue<MODE>(c, s, comp(c1, p), comp(c2, p), &inc[p]);
     }
-    if (x < L.nx) store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
+    if (x < L.nx) {
+      store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
+      if (MODE == MODE_INC)
+        store_masked(a.out2 + shot * a.out2_ss, colc + (long long)z * pl, make_float4(inc[0], inc[1], inc[2], inc[3]), x, L.nx);
+    }
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
@@ -278,7 +288,7 @@ cudaError_t launch_sweep3d_tma(int mode, const Layout& L, const Weights& W, cons
 // queue kernel above stays selectable with TP_SWEEP3D=plain for comparisons.
 cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& sa,
                            cudaStream_t s, int* err) {
-  const int kind = mode == MODE_STEP ? 0 : 1;  // TP_KERNEL_STENCIL / TP_KERNEL_IMAGING
+  const int kind = mode == MODE_IMAGE ? 1 : 0;  // TP_KERNEL_IMAGING / TP_KERNEL_STENCIL
   static const bool plain3d = [] {
     const char* e = getenv("TP_SWEEP3D");
     return e && strcmp(e, "plain") == 0;
@@ -289,14 +299,13 @@ cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const St
     e = launch_sweep3d_tma(mode, L, W, sa, s, err);
   } else {
     PlainArgs a{sa.src.ptr(L, 0), (long long)sa.src.fs * L.field, sa.p1.ptr(L, 0), (long long)sa.p1.fs * L.field,
-                sa.p2.ptr(L, 0), (long long)sa.p2.fs * L.field, sa.out, sa.out_ss, sa.nshots};
-    if (L.ndim == 3) {
-      if (W.R == 4) e = mode == MODE_STEP ? launch3d<4, MODE_STEP>(L, W, a, s) : launch3d<4, MODE_IMAGE>(L, W, a, s);
-      else e = mode == MODE_STEP ? launch3d<2, MODE_STEP>(L, W, a, s) : launch3d<2, MODE_IMAGE>(L, W, a, s);
-    } else {
-      if (W.R == 4) e = mode == MODE_STEP ? launch2d<4, MODE_STEP>(L, W, a, s) : launch2d<4, MODE_IMAGE>(L, W, a, s);
-      else e = mode == MODE_STEP ? launch2d<2, MODE_STEP>(L, W, a, s) : launch2d<2, MODE_IMAGE>(L, W, a, s);
-    }
+                sa.p2.ptr(L, 0), (long long)sa.p2.fs * L.field, sa.out, sa.out_ss, sa.nshots, sa.out2, sa.out2_ss};
+#define TP_DISPATCH(FN, RR)                                                   \
+  (mode == MODE_STEP ? FN<RR, MODE_STEP>(L, W, a, s)                          \
+                     : (mode == MODE_INC ? FN<RR, MODE_INC>(L, W, a, s) : FN<RR, MODE_IMAGE>(L, W, a, s)))
+    if (L.ndim == 3) e = W.R == 4 ? TP_DISPATCH(launch3d, 4) : TP_DISPATCH(launch3d, 2);
+    else e = W.R == 4 ? TP_DISPATCH(launch2d, 4) : TP_DISPATCH(launch2d, 2);
+#undef TP_DISPATCH
   }
   prof_after(kind, s);
   return e;

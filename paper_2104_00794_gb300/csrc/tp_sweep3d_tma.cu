@@ -1,8 +1,8 @@
 // 3-D leapfrog / imaging sweep with TMA-staged planes (sm_103a).
 //
 // Algorithm 1 lines 1 and 5 (operators f and f^T) are one 2k-order star
-// stencil per time step: out = 2u - u_old + c2 * S(u), S = 3 w0 u + sum_k w_k
-// (six neighbours at distance k).  The kernel is HBM-bound (16 B per point:
+// stencil per time step: out = 2u - u_old + c2 * S(u), S(u) = sum_k w_k times the
+// sum over the six neighbours at distance k of (neighbour - u).  The kernel is HBM-bound (16 B per point:
 // read u, u_old, c2; write out).  Design:
 //   * work = (x-y tile of 64 x 16 points, z plane) pairs of all shots, split
 //     evenly over a persistent grid (2 CTAs per SM); each CTA sweeps its
@@ -54,6 +54,8 @@ struct TmaArgs {
   int f_src, fs_src, f_p1, fs_p1, f_p2, fs_p2;
   float* out;
   long long out_ss;
+  float* out2;
+  long long out2_ss;
   int nshots, ntx, nty;
   long long work;
   int* err;
@@ -212,7 +214,6 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
   const int tx = tid & 15, ty = tid >> 4, lane = tid & 31;
   constexpr int RW = C::UW / 4;  // float4 per staged row
   const float4* U4 = reinterpret_cast<const float4*>(sU);
-  const float w0 = 3.0f * a.W.w[0];
   uint32_t ku = 0, kp = 0;
   bool ok = true;
   for (long long idx = start; idx < end && ok;) {
@@ -220,6 +221,7 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
     const int nzs = sg.z1 - sg.z0;
     const int x = sg.x0 + 4 * tx, y = sg.y0 + ty;
     float* out = a.out + sg.shot * a.out_ss;
+    float* out2 = MODE == MODE_INC ? a.out2 + sg.shot * a.out2_ss : nullptr;
     const int cidx = (ty + R) * RW + tx + 1;  // own float4 in a staged u plane
     float4 q[2 * R + 1];
     // prologue: planes z0-R .. z0+R-1 fill the queue; the first R are released
@@ -242,27 +244,36 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
       const float4* Uc = U4 + sc * (C::UFL / 4);
       const float4 xl = Uc[cidx - 1], xc = Uc[cidx], xr = Uc[cidx + 1];
       const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-      float s4[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) s4[p] = w0 * v[4 + p];
+      // difference form: S(u) = sum_k w_k sum_axes ((u[+k] - u) + (u[-k] - u)).  It equals
+      // w_0 * 3u + sum_k w_k (neighbours) for exact weights, but annihilates constants
+      // whatever the fp32 rounding of the weights (the plain sum form leaves a spurious
+      // zero-order term that makes long runs drift).
+      float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int k = 1; k <= R; ++k) {
         const float4 yp = Uc[cidx + k * RW], ym = Uc[cidx - k * RW];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-          const float t = (v[4 + p + k] + v[4 + p - k]) + (comp(yp, p) + comp(ym, p)) +
-                          (comp(q[R + k], p) + comp(q[R - k], p));
+          const float c = v[4 + p];
+          const float t = ((v[4 + p + k] - c) + (v[4 + p - k] - c)) + ((comp(yp, p) - c) + (comp(ym, p) - c)) +
+                          ((comp(q[R + k], p) - c) + (comp(q[R - k], p) - c));
           s4[p] = fmaf(a.W.w[k], t, s4[p]);
         }
       }
       const float4 c1 = reinterpret_cast<const float4*>(sP1 + sp * C::PFL)[ty * (BX / 4) + tx];
       const float4 c2 = reinterpret_cast<const float4*>(sP2 + sp * C::PFL)[ty * (BX / 4) + tx];
-      float res[4];
+      float res[4], inc[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const float c = v[4 + p];
-        res[p] = MODE == MODE_STEP ? fmaf(comp(c2, p), s4[p], 2.0f * c - comp(c1, p))
-                                   : fmaf(comp(c1, p), s4[p], comp(c2, p));
+        if (MODE == MODE_STEP) {
+          res[p] = fmaf(comp(c2, p), s4[p], 2.0f * c - comp(c1, p));
+        } else if (MODE == MODE_INC) {
+          inc[p] = fmaf(comp(c2, p), s4[p], comp(c1, p));
+          res[p] = c + inc[p];
+        } else {
+          res[p] = fmaf(comp(c1, p), s4[p], comp(c2, p));
+        }
       }
       __syncwarp();
       if (lane == 0) {
@@ -273,10 +284,14 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
         const long long o = a.L.off(sg.z0 + j, y, x);
         if (x + 3 < a.L.nx) {
           *reinterpret_cast<float4*>(out + o) = make_float4(res[0], res[1], res[2], res[3]);
+          if (MODE == MODE_INC) *reinterpret_cast<float4*>(out2 + o) = make_float4(inc[0], inc[1], inc[2], inc[3]);
         } else {
 #pragma unroll
           for (int p = 0; p < 4; ++p)
-            if (x + p < a.L.nx) out[o + p] = res[p];
+            if (x + p < a.L.nx) {
+              out[o + p] = res[p];
+              if (MODE == MODE_INC) out2[o + p] = inc[p];
+            }
         }
       }
 #pragma unroll
@@ -371,6 +386,8 @@ cudaError_t launch_t(const Layout& L, const Weights& W, const StencilArgs& a, cu
   t.f_p2 = a.p2.f0; t.fs_p2 = a.p2.fs;
   t.out = a.out;
   t.out_ss = a.out_ss;
+  t.out2 = a.out2;
+  t.out2_ss = a.out2_ss;
   t.nshots = a.nshots;
   t.ntx = (L.nx + BX - 1) / BX;
   t.nty = (L.ny + BY - 1) / BY;
@@ -388,8 +405,14 @@ cudaError_t launch_t(const Layout& L, const Weights& W, const StencilArgs& a, cu
 
 cudaError_t launch_sweep3d_tma(int mode, const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s,
                                int* err) {
-  if (W.R == 4) return mode == MODE_STEP ? launch_t<4, MODE_STEP>(L, W, a, s, err) : launch_t<4, MODE_IMAGE>(L, W, a, s, err);
-  return mode == MODE_STEP ? launch_t<2, MODE_STEP>(L, W, a, s, err) : launch_t<2, MODE_IMAGE>(L, W, a, s, err);
+  if (W.R == 4) {
+    if (mode == MODE_STEP) return launch_t<4, MODE_STEP>(L, W, a, s, err);
+    if (mode == MODE_INC) return launch_t<4, MODE_INC>(L, W, a, s, err);
+    return launch_t<4, MODE_IMAGE>(L, W, a, s, err);
+  }
+  if (mode == MODE_STEP) return launch_t<2, MODE_STEP>(L, W, a, s, err);
+  if (mode == MODE_INC) return launch_t<2, MODE_INC>(L, W, a, s, err);
+  return launch_t<2, MODE_IMAGE>(L, W, a, s, err);
 }
 
 }  // namespace tp

@@ -21,13 +21,14 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_ARG", 2: "TP_ERR_UNSTABLE", 3: "TP_ERR_NO
 PROBE_KINDS = {"rademacher": 0, "gaussian": 1, "identity": 2, "user": 3}
 OP_FORWARD, OP_ADJOINT, OP_GRADIENT_PROBED, OP_GRADIENT_FULL, OP_PROBED_FORWARD, OP_PROBED_BACKWARD = range(6)
 ACC_TYPES = {"f32": 0, "bf16": 1, "bf16_kahan": 2}
+TIME_FORMS = {"levels": 0, "increment": 1}
 KERNEL_KINDS = 6
 
 
 class tp_grid(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_float), ("dt", ctypes.c_float), ("nt", ctypes.c_int), ("order", ctypes.c_int),
-                ("vmax", ctypes.c_float)]
+                ("vmax", ctypes.c_float), ("form", ctypes.c_int)]
 
 
 class tp_geom(ctypes.Structure):

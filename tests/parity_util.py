@@ -14,8 +14,8 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def problem(w, nt=None):
-    return api.Problem.from_workload(w, nt=nt)
+def problem(w, nt=None, form="levels"):
+    return api.Problem.from_workload(w, nt=nt, form=form)
 
 
 def oracle_dobs(w, nt=None):
