@@ -59,11 +59,20 @@ Prof g_prof;
 
 }  // namespace
 
+// Under stream capture a plain event record only marks a dependency; the
+// external flag makes it a real record node of the graph, timed at replay.
+static void prof_record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
+
 void prof_before(int kind, cudaStream_t s) {
   if (!g_prof.on) return;
   std::lock_guard<std::mutex> lk(g_prof.m);
   if (!g_prof.on || g_prof.used + 2 > g_prof.ev.size()) return;
-  cudaEventRecord(g_prof.ev[g_prof.used], s);
+  prof_record(g_prof.ev[g_prof.used], s);
   g_prof.kind[g_prof.used / 2] = kind;
   g_prof.open = true;
 }
@@ -72,7 +81,7 @@ void prof_after(int, cudaStream_t s) {
   if (!g_prof.on) return;
   std::lock_guard<std::mutex> lk(g_prof.m);
   if (!g_prof.on || !g_prof.open) return;
-  cudaEventRecord(g_prof.ev[g_prof.used + 1], s);
+  prof_record(g_prof.ev[g_prof.used + 1], s);
   g_prof.used += 2;
   g_prof.open = false;
 }

@@ -1,12 +1,15 @@
 // 3-D leapfrog / imaging sweep with TMA-staged planes (sm_103a).
 //
 // Algorithm 1 lines 1 and 5 (operators f and f^T) are one 2k-order star
-// stencil per time step: out = 2u - u_old + c2 * S(u), S(u) = sum_k w_k times the
-// sum over the six neighbours at distance k of (neighbour - u).  The kernel is HBM-bound (16 B per point:
-// read u, u_old, c2; write out).  Design:
-//   * work = (x-y tile of 64 x 16 points, z plane) pairs of all shots, split
-//     evenly over a persistent grid (2 CTAs per SM); each CTA sweeps its
-//     contiguous run of planes in z (a run may span several tiles);
+// stencil per time step: out = 2u - u_old + c2 * S(u), S(u) = sum_k w_k times
+// the sum over the six neighbours at distance k of (neighbour - u).  The
+// kernel is HBM-bound (16 B per point: read u, u_old, c2; write out).  Design:
+//   * work items = (64 x 16 x-y tile, shot, z chunk); each tile column is cut
+//     into as many equal z chunks as keep one wave of 2 CTAs per SM busy, and
+//     items are ordered chunk-major, so neighbouring tiles are swept at the
+//     same depths at the same time and their shared halo planes hit in L2
+//     (a balanced linear split over (tile, z) left neighbours at different
+//     depths: the halo re-reads went to DRAM, 1.44x the algorithmic reads);
 //   * one producer thread streams, with cp.async.bulk.tensor (4-D tensor
 //     maps over the padded field families), the haloed u plane
 //     [16+2R][64+8] and the u_old / c2 planes [16][64] into a ring of shared
@@ -22,6 +25,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -32,13 +36,15 @@ namespace tp {
 
 namespace {
 
-constexpr int BX = 64, BY = 16, LA = 3;
-constexpr int NCONS = 256;                 // consumer threads (16 x 16)
+constexpr int NCONS = 256;                 // consumer threads, 4 x points each
 constexpr int NTHREADS = NCONS + 32;       // + one producer warp
 constexpr long long SPIN_LIMIT = 2000000000LL;  // cycles (~1 s)
 
-template <int R>
+// Tile BX x BY (BX/4 * BY == NCONS) and LA planes of lookahead.
+template <int R, int BX_, int BY_, int LA_>
 struct Cfg {
+  static constexpr int BX = BX_, BY = BY_, LA = LA_;
+  static_assert((BX / 4) * BY == NCONS, "one consumer thread per 4 points");
   static constexpr int NSU = R + 1 + LA;  // u stages
   static constexpr int NSP = LA + 1;      // u_old / c2 stages
   static constexpr int UW = BX + 8, UH = BY + 2 * R;
@@ -57,7 +63,8 @@ struct TmaArgs {
   float* out2;
   long long out2_ss;
   int nshots, ntx, nty;
-  long long work;
+  int nzc, zchunk;  // each tile column is cut into nzc chunks of zchunk planes
+  long long items;  // tiles x shots x nzc work items
   int* err;
 };
 
@@ -110,25 +117,29 @@ struct Seg {
   int shot, x0, y0, z0, z1;
 };
 
-__device__ __forceinline__ Seg segment(const TmaArgs& a, long long idx, long long end) {
-  const int nz = a.L.nz;
-  const long long item = idx / nz;
+// Work item -> (tile, shot, z chunk).  Items are ordered chunk-major, so a
+// wave of CTAs sweeps the same depths of neighbouring tiles at the same time
+// and the x/y halo planes one CTA reads are still in L2 for its neighbours.
+template <int BX, int BY>
+__device__ __forceinline__ Seg segment(const TmaArgs& a, long long item) {
+  const long long per = (long long)a.ntx * a.nty * a.nshots;
+  const int zc = (int)(item / per);
+  const long long rest = item % per;
   Seg s;
-  s.z0 = (int)(idx % nz);
-  s.z1 = (int)std::min<long long>(nz, s.z0 + (end - idx));
-  const int per = a.ntx * a.nty;
-  s.shot = (int)(item / per);
-  const int t = (int)(item % per);
+  s.shot = (int)(rest / ((long long)a.ntx * a.nty));
+  const int t = (int)(rest % ((long long)a.ntx * a.nty));
   s.x0 = (t % a.ntx) * BX;
   s.y0 = (t / a.ntx) * BY;
+  s.z0 = zc * a.zchunk;
+  s.z1 = min(a.L.nz, s.z0 + a.zchunk);
   return s;
 }
 
-template <int R, int MODE>
+template <int R, int MODE, class C>
 __global__ void __launch_bounds__(NTHREADS, 2)
 sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mP1,
             const __grid_constant__ CUtensorMap mP2, TmaArgs a) {
-  using C = Cfg<R>;
+  constexpr int BX = C::BX, BY = C::BY;
   extern __shared__ __align__(128) unsigned char smem[];
   float* sU = reinterpret_cast<float*>(smem);
   float* sP1 = sU + C::NSU * C::UFL;
@@ -153,18 +164,16 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
   }
   __syncthreads();
 
-  const long long per = a.work / gridDim.x, rem = a.work % gridDim.x;
-  const long long start = blockIdx.x * per + std::min<long long>(blockIdx.x, rem);
-  const long long end = start + per + (blockIdx.x < rem ? 1 : 0);
 
   if (tid >= NCONS) {
     // ------------------------------------------------------------ producer
     if (tid != NCONS) return;
     uint32_t ku = 0, kp = 0;
     bool ok = true;
-    for (long long idx = start; idx < end && ok;) {
-      const Seg sg = segment(a, idx, end);
+    for (long long item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
+      const Seg sg = segment<BX, BY>(a, item);
       const int nzs = sg.z1 - sg.z0;
+      if (nzs <= 0) continue;
       const int fu = a.f_src + sg.shot * a.fs_src, f1 = a.f_p1 + sg.shot * a.fs_p1, f2 = a.f_p2 + sg.shot * a.fs_p2;
       for (int k = 0; k < nzs + 2 * R && ok; ++k) {
         const int su = ku % C::NSU;
@@ -189,7 +198,6 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
           ++kp;
         }
       }
-      idx += nzs;
     }
     if (!ok) atomicOr(a.err, 1);
     // drain: wait (bounded) until every copy this thread issued has landed
@@ -211,14 +219,15 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
   }
 
   // -------------------------------------------------------------- consumers
-  const int tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+  const int tx = tid % (BX / 4), ty = tid / (BX / 4), lane = tid & 31;
   constexpr int RW = C::UW / 4;  // float4 per staged row
   const float4* U4 = reinterpret_cast<const float4*>(sU);
   uint32_t ku = 0, kp = 0;
   bool ok = true;
-  for (long long idx = start; idx < end && ok;) {
-    const Seg sg = segment(a, idx, end);
+  for (long long item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
+    const Seg sg = segment<BX, BY>(a, item);
     const int nzs = sg.z1 - sg.z0;
+    if (nzs <= 0) continue;
     const int x = sg.x0 + 4 * tx, y = sg.y0 + ty;
     float* out = a.out + sg.shot * a.out_ss;
     float* out2 = MODE == MODE_INC ? a.out2 + sg.shot * a.out2_ss : nullptr;
@@ -305,7 +314,6 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
     }
     ku += nzs + 2 * R;
     kp += nzs;
-    idx += nzs;
   }
   if (!ok && lane == 0) atomicOr(a.err, 1);
 }
@@ -367,12 +375,12 @@ bool get_map(const Layout& L, const FieldRef& f, int bw, int bh, CUtensorMap* ou
   return true;
 }
 
-template <int R, int MODE>
-cudaError_t launch_t(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
-  using C = Cfg<R>;
+template <int R, int MODE, class C>
+cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
+  constexpr int BX = C::BX, BY = C::BY;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(sweep3d_tma<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaFuncSetAttribute(sweep3d_tma<R, MODE, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     attr = true;
   }
   CUtensorMap mU, m1, m2;
@@ -391,14 +399,26 @@ cudaError_t launch_t(const Layout& L, const Weights& W, const StencilArgs& a, cu
   t.nshots = a.nshots;
   t.ntx = (L.nx + BX - 1) / BX;
   t.nty = (L.ny + BY - 1) / BY;
-  t.work = (long long)t.ntx * t.nty * a.nshots * L.nz;
   t.err = err;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long blocks = std::min<long long>(t.work, 2LL * sms);
-  sweep3d_tma<R, MODE><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, t);
+  // as many z chunks per tile column as keep one wave of 2 CTAs per SM busy
+  const long long cols = (long long)t.ntx * t.nty * a.nshots, slots = 2LL * sms;
+  t.nzc = (int)std::max<long long>(1, std::min<long long>(slots / cols, std::max(1, L.nz / (4 * R))));
+  t.zchunk = (L.nz + t.nzc - 1) / t.nzc;
+  t.nzc = (L.nz + t.zchunk - 1) / t.zchunk;
+  t.items = cols * t.nzc;
+  const long long blocks = std::min<long long>(t.items, slots);
+  sweep3d_tma<R, MODE, C><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, t);
   return cudaGetLastError();
+}
+
+// 64 x 16 tiles, 3 planes of lookahead: 128 x 8, 32 x 32 tiles measured the
+// same on GB300 and 4 planes of lookahead slower (2 CTAs per SM either way).
+template <int R, int MODE>
+cudaError_t launch_t(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
+  return launch_c<R, MODE, Cfg<R, 64, 16, 3>>(L, W, a, s, err);
 }
 
 }  // namespace
