@@ -182,6 +182,19 @@ tp_status tp_probed_backward(const tp_grid* grid, const tp_geom* geom, const tp_
                              int wrt_velocity, float* grad, double* gnorm, void* state,
                              size_t state_bytes, void* ws, size_t ws_bytes, void* stream);
 
+/* Range-finding probes of Eq. 6 for every shot: Q_s = qr(D_s D_s^T Z_s), where
+ * D_s = d_obs[s] is the observed record as an nt x nrec matrix (time x
+ * receivers) and Z_s the random probes that `probe` (kind RADEMACHER or
+ * GAUSSIAN, r <= 32, seed) draws for shot s.  Q: device [nshots][nt][r] fp32
+ * with orthonormal columns and diag(R) > 0 (computed in fp64: two reductions
+ * for D (D^T Z), then Gram-Schmidt applied twice).  Pass Q back as
+ * TP_PROBE_USER probes (scale 1).  ws: tp_qr_workspace_bytes(); a numerically
+ * rank-deficient record leaves zero columns and sets a flag that
+ * tp_workspace_status reports as TP_ERR_ARG. */
+size_t tp_qr_workspace_bytes(int nt, int nrec, int nshots, int r);
+tp_status tp_qr_probes(const tp_probe* probe, int nt, int nrec, int nshots, const float* d_obs, float* Q,
+                       void* ws, size_t ws_bytes, void* stream);
+
 /* The probing matrix that tp_gradient_probed draws for shot `shot`
  * (Eq. 1 probes from SplitMix64; Z[t][i], [nt][r], unscaled).  For
  * TP_PROBE_USER it copies the caller's Z. */

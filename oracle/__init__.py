@@ -16,6 +16,7 @@ the paper it follows in ``tp_oracle.c``:
                    second time difference folded into the probes)
   probes           Eq. 1 probing vectors from SplitMix64 (Rademacher,
                    Irwin-Hall Gaussian, identity)
+  qr_probes        Eq. 6 range-finding probes qr(D D^T Z) (numpy / LAPACK)
   fd_weights       Fornberg (1988) centred second-derivative weights
 """
 from __future__ import annotations
@@ -186,6 +187,19 @@ def probes(kind: str, nt: int, r: int, seed: int, shot: int = 0) -> np.ndarray:
     if _load().oracle_probes(PROBE_KINDS[kind], nt, r, ctypes.c_uint64(seed), shot, _dp(Z)) != 0:
         raise ValueError("bad probe specification")
     return Z
+
+
+def qr_probes(dobs_shot, Z):
+    """Range-finding probes of Eq. 6: [Q, ~] = qr(A Z) with A = D_obs D_obs^T,
+    D_obs the shot record as an nt x nrec matrix (time x receivers), Z the
+    nt x r random probes.  Householder QR (LAPACK) in fp64; the column signs
+    are fixed so that diag(R) > 0 (the QR factorisation is unique then)."""
+    D = np.asarray(dobs_shot, dtype=np.float64)
+    Y = D @ (D.T @ np.asarray(Z, dtype=np.float64))
+    Q, R = np.linalg.qr(Y)
+    sgn = np.sign(np.diag(R))
+    sgn[sgn == 0] = 1.0
+    return Q * sgn[None, :]
 
 
 def default_scale(kind: str, r: int) -> float:

@@ -186,6 +186,20 @@ class Problem:
                                   state.numel(), ws, n, _stream())
         return grad, gnorm
 
+    def qr_probes(self, d_obs, r: int, seed: int = 2104, kind: str = "rademacher") -> torch.Tensor:
+        """Range-finding probes of Eq. 6, [nshots, nt, r], from the observed
+        records; use them as ProbeSpec(kind="user", Z_user=Q, r=r)."""
+        d_obs = _f32(d_obs, self.device)
+        nt, nrec = self.nt, self.geom.nrec
+        spec = ProbeSpec(kind=kind, r=r, seed=seed)
+        n = native.tp_qr_workspace_bytes(nt, nrec, self.nshots, r)
+        buf = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+        ws = buf.data_ptr() + (-buf.data_ptr()) % 256
+        Q = torch.empty((self.nshots, nt, r), dtype=torch.float32, device=self.device)
+        native.tp_qr_probes(spec.to_c(), nt, nrec, self.nshots, _ptr(d_obs), _ptr(Q), ws, n, _stream())
+        native.tp_workspace_status(ws, n, _stream())
+        return Q
+
     def probes(self, probe: ProbeSpec, shot: int = 0, nt: Optional[int] = None):
         nt = self.nt if nt is None else nt
         Z = torch.empty((nt, probe.r), dtype=torch.float32, device=self.device)

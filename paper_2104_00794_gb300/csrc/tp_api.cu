@@ -711,6 +711,7 @@ tp_status tp_workspace_status(void* ws, size_t ws_bytes, void* stream) {
   TRY(cudaMemsetAsync(ws, 0, sizeof(int), st));
   if (flag & 1) return fail(TP_ERR_TIMEOUT, "a bounded device-side wait timed out");
   if (flag & 2) return fail(TP_ERR_ARG, "a source or receiver index lies outside the grid");
+  if (flag & 4) return fail(TP_ERR_ARG, "the record is numerically rank deficient for r range-finding probes");
   return TP_OK;
 }
 

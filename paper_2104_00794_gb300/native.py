@@ -70,6 +70,9 @@ def lib():
         L.tp_probes.argtypes = [Pr, i32, i32, vp, vp]
         L.tp_workspace_status.argtypes = [vp, sz, vp]
         L.tp_misfit_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+        L.tp_qr_workspace_bytes.argtypes = [i32, i32, i32, i32]
+        L.tp_qr_workspace_bytes.restype = sz
+        L.tp_qr_probes.argtypes = [Pr, i32, i32, i32, vp, vp, vp, sz, vp]
         L.tp_probed_state_bytes.argtypes = [G, E, Pr]
         L.tp_probed_state_bytes.restype = sz
         L.tp_probed_forward.argtypes = [G, E, Pr, vp, vp, vp, vp, sz, vp, sz, vp]
@@ -81,7 +84,7 @@ def lib():
         L.tp_kernel_name.restype = ctypes.c_char_p
         for f in ("tp_forward", "tp_adjoint", "tp_gradient_probed", "tp_gradient_full", "tp_probes",
                   "tp_workspace_status", "tp_profile_begin", "tp_profile_end", "tp_misfit_noalloc",
-                  "tp_probed_forward", "tp_probed_backward"):
+                  "tp_probed_forward", "tp_probed_backward", "tp_qr_probes"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
         return L
@@ -140,6 +143,17 @@ def tp_probed_backward(grid, geom, probe, vel, wavelet, adj_src, wrt_velocity, g
     _check(lib().tp_probed_backward(ctypes.byref(grid), ctypes.byref(geom), ctypes.byref(probe), vel, wavelet,
                                     adj_src, int(wrt_velocity), grad, gnorm, state, state_bytes, ws, ws_bytes,
                                     stream))
+
+
+def tp_qr_workspace_bytes(nt, nrec, nshots, r) -> int:
+    n = lib().tp_qr_workspace_bytes(nt, nrec, nshots, r)
+    if n == 0:
+        raise TprobeError(TP_ERR_ARG, "invalid sizes for range-finding probes")
+    return int(n)
+
+
+def tp_qr_probes(probe, nt, nrec, nshots, d_obs, Q, ws, ws_bytes, stream):
+    _check(lib().tp_qr_probes(ctypes.byref(probe), nt, nrec, nshots, d_obs, Q, ws, ws_bytes, stream))
 
 
 def tp_probes(probe, nt, shot, Z, stream):

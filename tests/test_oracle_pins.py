@@ -331,3 +331,44 @@ def test_probed_estimator_unbiased_with_closed_form_variance(kind, fourth):
     zsc = (est[keep] - gf[keep]) / sd[keep]
     assert 0.6 < np.mean(zsc ** 2) < 1.5, np.mean(zsc ** 2)
     assert np.mean(np.abs(zsc) > 4.5) < 0.01
+
+
+# ------------------------------------------------------------------ Eq. 6 (QR probes)
+def _record(nt=160, seed=4):
+    w = wl.small_2d(nx=61, nz=41, nt=nt, order=8, nrec=30)
+    return w, oracle.forward(oracle.grid_of(w), w.src[0], w.rec[0], w.vel_true, w.wavelet[0])
+
+
+def test_qr_probes_orthonormal_and_span_the_range():
+    w, D = _record()
+    r = 8
+    Z = oracle.probes("rademacher", w.nt, r, 5, 0)
+    Q = oracle.qr_probes(D, Z)
+    assert Q.shape == (w.nt, r)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(r), atol=1e-12)
+    Y = D @ (D.T @ Z)
+    assert np.linalg.norm(Y - Q @ (Q.T @ Y)) <= 1e-10 * np.linalg.norm(Y)
+    P = Q @ Q.T
+    np.testing.assert_allclose(P @ P, P, atol=1e-12)           # an orthogonal projector
+    # R = Q^T Y is upper triangular with a positive diagonal (sign convention)
+    R = Q.T @ Y
+    assert np.all(np.abs(np.tril(R, -1)) <= 1e-10 * np.abs(R).max()) and np.all(np.diag(R) > 0)
+
+
+def test_qr_probes_capture_the_dominant_range():
+    """The range finder approximates the span of the top singular vectors of
+    D D^T (Halko et al.): with r a few above the numerical rank of a low-rank
+    record, Q spans it to rounding; random +-1 probes of the same r carry the
+    identity's cross-talk instead."""
+    rng = np.random.default_rng(2)
+    nt, nrec, k, r = 200, 40, 5, 12
+    U = np.linalg.qr(rng.standard_normal((nt, k)))[0]
+    D = U @ np.diag([50.0, 20.0, 10.0, 5.0, 2.0]) @ rng.standard_normal((k, nrec))
+    Q = oracle.qr_probes(D, oracle.probes("rademacher", nt, r, 9, 0))
+    assert np.linalg.norm(U - Q @ (Q.T @ U)) <= 1e-10
+    # trace of D D^T estimated with the QR probes (scale 1) is exact here,
+    # with Rademacher probes (scale 1/r) it is not
+    A = D @ D.T
+    assert np.trace(Q.T @ A @ Q) == pytest.approx(np.trace(A), rel=1e-10)
+    Zr = oracle.probes("rademacher", nt, r, 9, 0)
+    assert abs(np.trace(Zr.T @ A @ Zr) / r - np.trace(A)) > 1e-3 * np.trace(A)
