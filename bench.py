@@ -16,6 +16,7 @@ updates / the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -48,6 +49,9 @@ def parse():
     ap.add_argument("--r", type=int, default=32)
     ap.add_argument("--T", type=int, default=32)
     ap.add_argument("--form", default="levels", choices=["levels", "increment"], help="fp32 time-stepping form")
+    ap.add_argument("--acc", default="f32", choices=["f32", "bf16", "bf16_kahan", "f32_fold"],
+                    help="probe accumulator storage of the headline gradient")
+    ap.add_argument("--no-fold", action="store_true", help="skip the single-accumulator comparison")
     ap.add_argument("--no-full", action="store_true", help="skip the full-storage comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -297,7 +301,7 @@ def main():
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     vel_true, vel0, wav = dev(w.vel_true), dev(w.vel0), dev(w.wavelet)
     d_obs = p.forward(vel_true, wav).clone()  # observed data of the true model (setup, untimed)
-    probe = api.ProbeSpec(kind=w.probe_kind, r=w.r, T=w.T, seed=w.seed)
+    probe = api.ProbeSpec(kind=w.probe_kind, r=w.r, T=w.T, seed=w.seed, acc=args.acc)
     grad = torch.empty(p.shape, dtype=torch.float32, device="cuda")
     scal = torch.empty(2, dtype=torch.float64, device="cuda")
     pts = 2.0 * w.N * w.nt * w.nshots  # grid-point updates per gradient (fwd + adj)
@@ -376,6 +380,24 @@ def main():
     gemm_bytes = gemm_pts * 4 * (w.T + 2 * w.r)
     gemm_flops = 2.0 * gemm_pts * w.T * w.r * 2  # hi and lo products (Rademacher probes exact in tf32)
     launches = sum(v["launches"] for v in kern.values())
+
+    # ---- single-accumulator form (one N r set, vbar folded into the gradient)
+    fold = None
+    if not args.no_fold and args.acc == "f32" and w.r <= 32:
+        fprobe = dataclasses.replace(probe, acc="f32_fold")
+        run_fold = lambda: p.gradient_probed(vel0, wav, d_obs, fprobe, grad=grad, scalars=scal)
+        fdms, fdkern = graph_timed(run_fold)
+        fdms = max_over_ranks(fdms)
+        p.status(native.OP_GRADIENT_PROBED)
+        rel = float((grad.double() - grad_probed.double()).norm() / grad_probed.double().norm())
+        fg = fdkern.get("probe_gemm_tcgen05", {"ms": 0.0, "launches": 0})
+        fold = {"value": pts * world / (fdms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_step": fdms,
+                "workspace_bytes": p.workspace_bytes(native.OP_GRADIENT_PROBED, fprobe),
+                "accumulator_values": mem["probed_accumulator_values"] // 2,
+                "rel_l2_vs_two_sets": rel,
+                "gemm_ms_per_launch": fg["ms"] / max(fg["launches"], 1),
+                "kernels": {k: v for k, v in fdkern.items() if v["launches"]}}
+        p.release()
 
     # ---- full-storage gradient of the same problem
     full = None
@@ -468,6 +490,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "memory": mem,
+            "single_accumulator": fold,
             "full_storage": full,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -73,8 +73,17 @@ typedef enum {
 typedef enum {
   TP_ACC_F32 = 0,         /* fp32: 4 B per value */
   TP_ACC_BF16 = 1,        /* bf16, round to nearest: 2 B per value */
-  TP_ACC_BF16_KAHAN = 2   /* bf16 value + bf16 compensation (the rounding error of
+  TP_ACC_BF16_KAHAN = 2,  /* bf16 value + bf16 compensation (the rounding error of
                              the stored value, carried to the next window): 4 B */
+  TP_ACC_F32_FOLD = 3     /* one accumulator set (N r values instead of 2 N r, the
+                             single-accumulator form of Algorithm 1 line 8): the
+                             forward accumulators are fp32; before the adjoint
+                             they are turned into ubar_i in place, and each adjoint
+                             window's Q_w^T lambda is folded straight into the
+                             gradient, g += sum_i ubar_i (Q_w^T lambda)_i, so vbar
+                             is never stored.  Needs r <= 32.  tp_probed_backward
+                             then overwrites the state's accumulators (the state
+                             serves one backward call). */
 } tp_acc;
 
 /* Grid and time axis.  Eq. 2 (F(m; q) on this grid). */
@@ -116,7 +125,7 @@ typedef struct {
   const float* Z_user; /* device [nshots][nt][r] when kind == TP_PROBE_USER */
   float scale;         /* estimator scale; 0 selects the default: 1/r for
                           random probes (Eq. 1), 1 for IDENTITY and USER */
-  int acc;             /* tp_acc storage of the accumulators; BF16 kinds need r <= 32 */
+  int acc;             /* tp_acc storage of the accumulators; all but F32 need r <= 32 */
 } tp_probe;
 
 /* Bytes of device workspace that `op` needs (0 on invalid arguments; see

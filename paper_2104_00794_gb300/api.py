@@ -44,7 +44,7 @@ class ProbeSpec:
     seed: int = 2104
     scale: float = 0.0
     Z_user: Optional[torch.Tensor] = None
-    acc: str = "f32"  # accumulator storage: "f32", "bf16", "bf16_kahan"
+    acc: str = "f32"  # accumulator storage: "f32", "bf16", "bf16_kahan", "f32_fold" (one set, r <= 32)
 
     def to_c(self) -> native.tp_probe:
         return native.tp_probe(native.PROBE_KINDS[self.kind], int(self.r), int(self.T), int(self.seed) & (2**64 - 1),

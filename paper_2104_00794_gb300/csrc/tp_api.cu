@@ -173,8 +173,9 @@ tp_status check_geom(const tp_geom* g) {
 
 tp_status check_probe(const tp_probe* p, int nt) {
   if (!p) return fail(TP_ERR_ARG, "probe is NULL");
-  if (p->acc < TP_ACC_F32 || p->acc > TP_ACC_BF16_KAHAN) return fail(TP_ERR_ARG, "unknown accumulator type %d", p->acc);
-  if (p->acc != TP_ACC_F32 && p->r > 32) return fail(TP_ERR_ARG, "bf16 accumulators need r <= 32 (got %d)", p->r);
+  if (p->acc < TP_ACC_F32 || p->acc > TP_ACC_F32_FOLD) return fail(TP_ERR_ARG, "unknown accumulator type %d", p->acc);
+  if (p->acc != TP_ACC_F32 && p->r > 32)
+    return fail(TP_ERR_ARG, "bf16 and folded accumulators need r <= 32 (got %d)", p->r);
   if (p->kind < 0 || p->kind > 3) return fail(TP_ERR_ARG, "unknown probe kind %d", p->kind);
   if (p->r < 1 || p->r > 256) return fail(TP_ERR_ARG, "r must be in 1..256 (got %d)", p->r);
   if (p->kind == TP_PROBE_IDENTITY && p->r != nt) return fail(TP_ERR_ARG, "identity probes need r == nt");
@@ -226,7 +227,7 @@ tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe
       P->acc = pr->acc;
       P->scale = pr->scale > 0.f ? pr->scale
                                  : ((pr->kind == TP_PROBE_RADEMACHER || pr->kind == TP_PROBE_GAUSSIAN) ? 1.0f / pr->r : 1.0f);
-      P->acc_esize = P->acc == TP_ACC_F32 ? 4 : 2;
+      P->acc_esize = (P->acc == TP_ACC_F32 || P->acc == TP_ACC_F32_FOLD) ? 4 : 2;
       P->acc_elems = (long long)P->r * P->L.field * (P->acc == TP_ACC_BF16_KAHAN ? 2 : 1);
       const size_t accb = (size_t)ns * P->acc_elems * P->acc_esize;  // one accumulator set, all shots
       size_t sc = 0;
@@ -236,10 +237,11 @@ tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe
       P->nf = (long long)P->S * ns;
       P->o_f = take(cur, (size_t)P->nf * fb);  // ring of T+2 levels
       if (op != TP_OP_PROBED_FORWARD) {
-        P->o_V = take(cur, accb);
+        if (P->acc != TP_ACC_F32_FOLD) P->o_V = take(cur, accb);  // vbar (the folded form keeps none)
         P->o_qbar = take(cur, (size_t)ns * P->nsrc * P->r * sizeof(float));
         P->o_gacc = take(cur, (size_t)ns * fb);
-        if (P->acc != TP_ACC_F32) P->o_conv = take(cur, (size_t)2 * ns * fb);  // fp32 copies of P_i, V_i
+        if (P->acc == TP_ACC_BF16 || P->acc == TP_ACC_BF16_KAHAN)
+          P->o_conv = take(cur, (size_t)2 * ns * fb);  // fp32 copies of P_i, V_i
       }
       if (op == TP_OP_GRADIENT_PROBED) {
         P->o_state = take(cur, P->state_bytes);
@@ -485,7 +487,8 @@ GemmArgs gemm_args(const Ctx& c, float* Q) {
   GemmArgs g{};
   g.ring = c.at<float>(P.o_f); g.slot_stride = P.L.field; g.ring_ss = (long long)P.S * P.L.field; g.nslots = P.S;
   g.Q = Q; g.nt = P.nt; g.r = P.r; g.q_ss = (long long)P.nt * P.r;
-  g.L = P.L; g.pstride = P.L.field; g.p_ss = P.acc_elems; g.acc = P.acc;
+  g.L = P.L; g.pstride = P.L.field; g.p_ss = P.acc_elems;
+  g.acc = P.acc == TP_ACC_F32_FOLD ? TP_ACC_F32 : P.acc;  // the folded form accumulates ubar in fp32
   g.nshots = P.nshots; g.qlo = 2; g.qhi = P.nt - 1;
   g.q_has_lo = (P.kind == TP_PROBE_GAUSSIAN || P.kind == TP_PROBE_USER) ? 1 : 0;
   g.err = c.err();
@@ -526,10 +529,66 @@ tp_status probed_forward_impl(const Ctx& c, const tp_probe* probe, const float* 
 // Algorithm 1 lines 4-8: adjoint sweep driven by s (all shots), vbar_i =
 // sum_{k=2}^{nt-1} Q[k, i] lambda[k], then grad = -scale sum_i ubar_i vbar_i
 // (dJ/dm, or dJ/dv when wrt_velocity) and its fp64 norm.
+// Single-accumulator form (TP_ACC_F32_FOLD): ubar_i = c2 S(P_i) + dt^2 v^2 S^T qbar_i
+// (= dt^2 v^2 (L P_i + S^T qbar_i)) replaces P_i in place; the adjoint windows
+// fold sum_i ubar_i (Q_w^T lambda)_i into one accumulator field per shot, and
+// grad = -(scale / dt^2) sum_s of it.  Same estimator as the two-set form.
+tp_status probed_backward_fold(const Ctx& c, const tp_grid* grid, const float* vel, const float* wavelet,
+                               const float* s, int wrt_velocity, float* grad, double* gnorm, const float* Q,
+                               float* Pacc) {
+  const Plan& P = c.P;
+  const size_t fb = (size_t)P.L.field * sizeof(float);
+  const int nt = P.nt, T = P.T, S = P.S, r = P.r;
+  const Fam fG{P.o_gacc, P.nshots, 1};
+  float* tmp = c.ptr(fG, 0);  // scratch for ubar_i until the adjoint needs the accumulator
+  TRY(launch_qbar(Q, nt, r, wavelet, P.nsrc, P.nshots, 1, nt - 2, 1, c.at<float>(P.o_qbar), c.st));
+  const FieldRef fPr{Pacc, (int)(P.nshots * (long long)r), 0, r};
+  const FieldRef c2 = c.ref(Fam{P.o_c2, 1, 0}, 0);
+  for (int i = 0; i < r; ++i) {
+    FieldRef pi = fPr;
+    pi.f0 = i;
+    TRY(cudaMemsetAsync(tmp, 0, (size_t)P.nshots * fb, c.st));
+    StencilArgs a{pi, c2, c.ref(fG, 0), tmp, c.ss(fG), P.nshots};
+    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
+    TRY(cudaMemcpy2DAsync(Pacc + (long long)i * P.L.field, (size_t)P.acc_elems * sizeof(float), tmp, fb, fb,
+                          P.nshots, cudaMemcpyDeviceToDevice, c.st));
+  }
+  TRY(launch_source_into_acc(c.at<long long>(P.o_soff), c.at<float>(P.o_cs), c.at<float>(P.o_qbar), P.nsrc,
+                             P.nshots, r, Pacc, P.acc_elems, P.L.field, c.st));
+  TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));  // levels nt, nt+1 start at zero
+  TRY(cudaMemsetAsync(tmp, 0, (size_t)P.nshots * fb, c.st));
+  const Fam ring{P.o_f, (int)P.nf, S};
+  auto level = [S](int t) { return t % S; };
+  GemmArgs g = gemm_args(c, const_cast<float*>(Q));
+  g.P = Pacc;
+  g.acc = 3;  // dot epilogue
+  g.G = tmp;
+  g.g_ss = P.L.field;
+  g.qshift = 0;
+  auto adj_after = [&](int lev) -> tp_status {
+    const int top = nt - 1 - ((nt - 1 - lev) / T) * T;
+    const int bottom = std::max(2, top - T + 1);
+    if (lev == bottom) {
+      g.level0 = bottom;
+      g.nlev = top - bottom + 1;
+      TRY(launch_probe_gemm(g, c.st));
+    }
+    return TP_OK;
+  };
+  TRYS(adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after));
+  TRY(launch_finish_grad(P.L, vel, tmp, P.nshots, P.L.field, P.scale / (grid->dt * grid->dt), grad, c.st, 0));
+  if (wrt_velocity) TRY(launch_chain_velocity(vel, grad, (long long)P.L.nx * P.L.ny * P.L.nz, c.st));
+  TRYS(grad_norm(c, grad, gnorm));
+  return TP_OK;
+}
+
 tp_status probed_backward_impl(const Ctx& c, const tp_grid* grid, const tp_geom* geom, const float* vel,
                                const float* wavelet, const float* s, int wrt_velocity, float* grad, double* gnorm,
                                const float* Q, const void* Pacc) {
   const Plan& P = c.P;
+  if (P.acc == TP_ACC_F32_FOLD)
+    return probed_backward_fold(c, grid, vel, wavelet, s, wrt_velocity, grad, gnorm, Q,
+                                static_cast<float*>(const_cast<void*>(Pacc)));
   const size_t fb = (size_t)P.L.field * sizeof(float);
   const int nt = P.nt, T = P.T, S = P.S, r = P.r;
   TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));  // levels nt, nt+1 start at zero

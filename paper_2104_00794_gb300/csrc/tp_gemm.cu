@@ -317,11 +317,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 __device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
-// ACC: accumulator storage (0 fp32, 1 bf16, 2 bf16 value + bf16 compensation)
+// ACC: accumulator storage (0 fp32, 1 bf16, 2 bf16 value + bf16 compensation),
+// or 3: dot mode -- the staged rows are the r forward fields ubar (fp32) and
+// the gradient row, and the tile is folded into the gradient at once.
 template <int KP, int ACC>
 struct GCfg {
-  static constexpr uint32_t PROW = ACC == 0 ? TILE_M * 4 : TILE_M * 2;   // bytes of one staged row
-  static constexpr uint32_t PBYTES = GRP * PROW * (ACC == 2 ? 2 : 1);   // accumulator part of a stage
+  static constexpr uint32_t PROW = (ACC == 0 || ACC == 3) ? TILE_M * 4 : TILE_M * 2;  // bytes of one staged row
+  static constexpr uint32_t PBYTES = GRP * PROW * (ACC == 2 ? 2 : 1) + (ACC == 3 ? PROW : 0);
   static constexpr uint32_t STAGE = (uint32_t)KP * TILE_M * 4 + PBYTES;  // A rows then accumulator rows
   static constexpr uint32_t ABYTES = TILE_M * KP * 4;
   static constexpr uint32_t BBYTES = GRP * KP * 4;
@@ -388,7 +390,7 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
 
   if (warp == GW) {
     // ------------------------------------------------------------ producer warp
-    const int ncp = ACC == 2 ? 2 * a.r : a.r;  // accumulator rows copied per tile
+    const int ncp = ACC == 2 ? 2 * a.r : (ACC == 3 ? a.r + 1 : a.r);  // accumulator rows copied per tile
     const uint32_t bytes = (uint32_t)a.nlev * TILE_M * 4 + (uint32_t)ncp * C::PROW;
     bool ok = true;
     uint32_t it = 0;
@@ -410,7 +412,9 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
           bulk_g2s(dst + (uint32_t)c * TILE_M * 4, ring + (long long)sl * a.slot_stride + base, TILE_M * 4, full + 8 * s);
         } else {
           const int idx = c - a.nlev;
-          if (ACC == 0) {
+          if (ACC == 3 && idx == a.r) {  // the gradient row, staged after GRP field rows
+            bulk_g2s(pdst + (uint32_t)GRP * C::PROW, a.G + shot * a.g_ss + base, C::PROW, full + 8 * s);
+          } else if (ACC == 0 || ACC == 3) {
             bulk_g2s(pdst + (uint32_t)idx * C::PROW, Pf + (long long)idx * a.pstride + base, C::PROW, full + 8 * s);
           } else if (ACC == 1 || idx < a.r) {  // bf16 values
             bulk_g2s(pdst + (uint32_t)idx * C::PROW, Ph + (long long)idx * a.pstride + base, C::PROW, full + 8 * s);
@@ -460,17 +464,18 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
         *reinterpret_cast<float4*>(A_lo + o) = lo;
       }
       // 2. old accumulators of this point, then release the stage
-      float pold[GRP];
+      float pold[GRP];  // old accumulators, or the forward fields in dot mode
 #pragma unroll
       for (int i = 0; i < GRP; ++i) {
         float v = 0.f;
         if (i < a.r) {
-          if (ACC == 0) v = sP[i * TILE_M + tid];
+          if (ACC == 0 || ACC == 3) v = sP[i * TILE_M + tid];
           else v = __bfloat162float(sPh[i * TILE_M + tid]);
           if (ACC == 2) v += __bfloat162float(sPh[(GRP + i) * TILE_M + tid]);
         }
         pold[i] = v;
       }
+      const float gold = ACC == 3 ? sP[GRP * TILE_M + tid] : 0.f;
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + 8 * s);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -500,6 +505,7 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long prow = tile_base(tile) + tid;
       const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      float dot = 0.f;
 #pragma unroll
       for (int c = 0; c < GRP / 16; ++c) {
         if (c * 16 < NP) {
@@ -508,7 +514,9 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int i = c * 16 + j;
-            if (i < a.r) {
+            if (ACC == 3) {
+              if (i < a.r) dot = fmaf(pold[i], acc[j], dot);
+            } else if (i < a.r) {
               const float nv = pold[i] + acc[j];
               if (ACC == 0) {
                 Pf[(long long)i * a.pstride + prow] = nv;
@@ -522,6 +530,7 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
           }
         }
       }
+      if (ACC == 3) a.G[shot * a.g_ss + prow] = gold + dot;
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     if (!ok && tid == 0) atomicOr(a.err, 1);
@@ -592,11 +601,13 @@ cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
     return (e && strcmp(e, "regs") == 0) ? 1 : 0;
   }();
   cudaError_t e;
-  if (a.acc != 0 || (a.r <= GRP && variant == 0)) {  // bf16 storage exists on this path only (r <= 32)
+  if (a.acc != 0 || (a.r <= GRP && variant == 0)) {  // bf16 storage and dot mode exist on this path only (r <= 32)
     if (a.nlev <= 32)
-      e = a.acc == 0 ? launch_tma<32, 0>(a, s) : (a.acc == 1 ? launch_tma<32, 1>(a, s) : launch_tma<32, 2>(a, s));
+      e = a.acc == 0 ? launch_tma<32, 0>(a, s)
+                     : (a.acc == 1 ? launch_tma<32, 1>(a, s) : (a.acc == 2 ? launch_tma<32, 2>(a, s) : launch_tma<32, 3>(a, s)));
     else
-      e = a.acc == 0 ? launch_tma<64, 0>(a, s) : (a.acc == 1 ? launch_tma<64, 1>(a, s) : launch_tma<64, 2>(a, s));
+      e = a.acc == 0 ? launch_tma<64, 0>(a, s)
+                     : (a.acc == 1 ? launch_tma<64, 1>(a, s) : (a.acc == 2 ? launch_tma<64, 2>(a, s) : launch_tma<64, 3>(a, s)));
   } else if (a.nlev <= 32) {
     e = a.r <= 16 ? launch_kp<32, 16>(a, s) : (a.r <= 32 ? launch_kp<32, 32>(a, s) : launch_kp<32, 0>(a, s));
   } else {

@@ -99,7 +99,8 @@ struct GemmArgs {
   int level0, nlev, qshift, qlo, qhi;
   const float* Q; int nt, r; long long q_ss;
   void* P; long long pstride; long long p_ss;  // P[s][i] at P + s*p_ss + i*pstride
-  int acc;
+  int acc;                 // 3: dot mode, G[s][x] += sum_i P[s][i][x] * tile[x, i] (P fp32, read only)
+  float* G; long long g_ss;
   int nshots;
   int q_has_lo;
   int* err;
@@ -142,9 +143,13 @@ cudaError_t launch_sumsq(const float* a, long long n, double* part, int nblk, cu
 // out = scale * sum(part[0..nblk))  (fixed order; sqrt first if asked; NaN if *err & 1)
 cudaError_t launch_finalize_sum(const double* part, int nblk, double scale, double* out,
                                 int sqrt_result, const int* err, cudaStream_t s);
-// grad[x] = -scale_h2 * vel[x]^2 * sum_s gacc[s][off(x)]
+// grad[x] = -scale_h2 * vel[x]^2 * sum_s gacc[s][off(x)]   (times_v2 = 1)
+// grad[x] = -scale_h2 * sum_s gacc[s][off(x)]              (times_v2 = 0)
 cudaError_t launch_finish_grad(const Layout& L, const float* vel, const float* gacc, int nshots,
-                               long long gacc_ss, float scale_h2, float* grad, cudaStream_t s);
+                               long long gacc_ss, float scale_h2, float* grad, cudaStream_t s, int times_v2 = 1);
+// U[s][i][src_off[s][k]] += cinj[s][k] * qbar[s][k][i]   (serial, fixed order)
+cudaError_t launch_source_into_acc(const long long* src_off, const float* cinj, const float* qbar, int nsrc,
+                                   int nshots, int r, float* U, long long u_ss, long long field, cudaStream_t s);
 // fp32 copy of accumulator field i of every shot: out[s] = value (+ compensation)
 cudaError_t launch_acc_to_f32(const void* P, int acc, int r, int i, long long field, int nshots, float* out,
                               long long out_ss, cudaStream_t s);

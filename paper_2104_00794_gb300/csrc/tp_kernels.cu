@@ -166,15 +166,29 @@ __global__ void __launch_bounds__(RED_THREADS) finalize_kernel(const double* __r
 
 // grad[x] = -scale_h2 * vel[x]^2 * sum_s gacc[s][off(x)]
 __global__ void finish_grad_kernel(Layout L, const float* __restrict__ vel, const float* __restrict__ gacc,
-                                   int nshots, long long gacc_ss, float scale_h2, float* __restrict__ grad) {
+                                   int nshots, long long gacc_ss, float scale_h2, float* __restrict__ grad,
+                                   int times_v2) {
   const long long n = (long long)L.nx * L.ny * L.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long o = L.off_flat(i);
     float acc = 0.f;
     for (int s = 0; s < nshots; ++s) acc += gacc[s * gacc_ss + o];
-    const float v = vel[i];
+    const float v = times_v2 ? vel[i] : 1.0f;
     grad[i] = -scale_h2 * v * v * acc;
   }
+}
+
+__global__ void source_into_acc_kernel(const long long* __restrict__ soff, const float* __restrict__ cinj,
+                                       const float* __restrict__ qbar, int nsrc, int nshots, int r,
+                                       float* __restrict__ U, long long u_ss, long long field) {
+  const int i = threadIdx.x;  // one thread per probe column, shots and sources in a fixed order
+  if (i >= r || blockIdx.x != 0) return;
+  for (int s = 0; s < nshots; ++s)
+    for (int k = 0; k < nsrc; ++k) {
+      const long long o = soff[(long long)s * nsrc + k];
+      if (o < 0) continue;
+      U[s * u_ss + (long long)i * field + o] += cinj[(long long)s * nsrc + k] * qbar[((long long)s * nsrc + k) * r + i];
+    }
 }
 
 __global__ void qbar_kernel(const float* __restrict__ Q, int nt, int r, const float* __restrict__ wav, int nsrc,
@@ -311,11 +325,19 @@ cudaError_t launch_finalize_sum(const double* part, int nblk, double scale, doub
   return cudaGetLastError();
 }
 
+cudaError_t launch_source_into_acc(const long long* src_off, const float* cinj, const float* qbar, int nsrc,
+                                   int nshots, int r, float* U, long long u_ss, long long field, cudaStream_t s) {
+  prof_before(5, s);
+  source_into_acc_kernel<<<1, 64, 0, s>>>(src_off, cinj, qbar, nsrc, nshots, r, U, u_ss, field);
+  prof_after(5, s);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finish_grad(const Layout& L, const float* vel, const float* gacc, int nshots, long long gacc_ss,
-                               float scale_h2, float* grad, cudaStream_t s) {
+                               float scale_h2, float* grad, cudaStream_t s, int times_v2) {
   prof_before(5, s);
   const long long n = (long long)L.nx * L.ny * L.nz;
-  finish_grad_kernel<<<grid_for(n, 256), 256, 0, s>>>(L, vel, gacc, nshots, gacc_ss, scale_h2, grad);
+  finish_grad_kernel<<<grid_for(n, 256), 256, 0, s>>>(L, vel, gacc, nshots, gacc_ss, scale_h2, grad, times_v2);
   prof_after(5, s);
   return cudaGetLastError();
 }

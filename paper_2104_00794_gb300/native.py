@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_ARG", 2: "TP_ERR_UNSTABLE", 3: "TP_ERR_NO
                 5: "TP_ERR_TIMEOUT"}
 PROBE_KINDS = {"rademacher": 0, "gaussian": 1, "identity": 2, "user": 3}
 OP_FORWARD, OP_ADJOINT, OP_GRADIENT_PROBED, OP_GRADIENT_FULL, OP_PROBED_FORWARD, OP_PROBED_BACKWARD = range(6)
-ACC_TYPES = {"f32": 0, "bf16": 1, "bf16_kahan": 2}
+ACC_TYPES = {"f32": 0, "bf16": 1, "bf16_kahan": 2, "f32_fold": 3}
 TIME_FORMS = {"levels": 0, "increment": 1}
 KERNEL_KINDS = 6
 

@@ -66,6 +66,27 @@ def test_workspace_sizes_follow_the_memory_model(L):
     assert fwd < probed / 10
 
 
+def test_folded_accumulators_halve_the_accumulator_memory(L):
+    """TP_ACC_F32_FOLD keeps one N r accumulator set instead of two: the
+    probed workspace drops by exactly the vbar block (nshots r padded
+    fields), the state is unchanged, and r > 32 is rejected."""
+    w = wl.config3()
+    g, geo = _grid(w), _geom(w)
+    r = 16
+    two = native.tp_probe(0, r, 32, 1, None, 0.0, native.ACC_TYPES["f32"])
+    one = native.tp_probe(0, r, 32, 1, None, 0.0, native.ACC_TYPES["f32_fold"])
+    for op in (native.OP_GRADIENT_PROBED, native.OP_PROBED_BACKWARD):
+        b2 = native.tp_workspace_bytes(op, g, geo, two)
+        b1 = native.tp_workspace_bytes(op, g, geo, one)
+        vbar = b2 - b1
+        # one padded field per probe and shot, 4 bytes per value
+        assert w.nshots * r * 4 * w.N <= vbar <= 1.25 * w.nshots * r * 4 * w.N
+    assert (native.tp_probed_state_bytes(g, geo, two) == native.tp_probed_state_bytes(g, geo, one))
+    big = native.tp_probe(0, 33, 32, 1, None, 0.0, native.ACC_TYPES["f32_fold"])
+    n = L.tp_workspace_bytes(native.OP_GRADIENT_PROBED, ctypes.byref(g), ctypes.byref(geo), ctypes.byref(big))
+    assert n == 0 and "r <= 32" in native.last_error()
+
+
 @pytest.mark.parametrize("mutate,msg", [
     (lambda g, p: setattr(g, "ndim", 4), "ndim"),
     (lambda g, p: setattr(g, "order", 6), "order"),
