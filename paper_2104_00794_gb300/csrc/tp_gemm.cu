@@ -271,18 +271,30 @@ probe_gemm_tf32(GemmArgs a, int NP, int ncols, long long ntiles) {
   }
 }
 
-// ------------------------------------------------------------------ TMA variant
-// For r <= 32: a producer warp streams each tile's window rows (nlev x 512 B)
-// and old accumulator rows (r x 512 B) into a 2-stage shared-memory ring with
-// cp.async.bulk (completion counted on an mbarrier); four worker warps split
-// the snapshots into tf32 hi/lo operands, one thread issues the MMAs, and the
-// workers add the TMEM tile to the staged accumulators and store them.  Two
-// CTAs per SM (KP = 32) keep four tiles of copies in flight per SM without
-// holding them in registers.
-constexpr int GNS = 2;      // stages
-constexpr int GRP = 32;     // accumulator rows staged per tile (r <= 32)
-constexpr int GW = 4;       // worker warps
-constexpr int GTHREADS = (GW + 1) * 32;
+// ------------------------------------------------------------ pipelined variant
+// For r <= 32 (every accumulator kind and the dot mode) the window GEMM runs
+// as a warp-specialised pipeline, one CTA per SM looping over 128-point tiles:
+//   warp 0      producer of the window rows: per tile one or two 4-D TMA
+//               tensor copies (nlev x 512 B; two where the ring wraps) into
+//               NSR snapshot stages;
+//   warp 10     producer of the old accumulator rows (and, in dot mode, the
+//               gradient row): one or two TMA copies into NSA stages;
+//   warp 1      allocates TMEM; one lane issues the tcgen05 MMAs of tile k
+//               into TMEM buffer k % 2 and commits them to mdone[k % 2];
+//   warps 2-5   converters: split tile k's snapshots into tf32 hi/lo operand
+//               buffers (NA of them) in the K-major core-matrix layout;
+//   warps 6-9   epilogue: read tile k's accumulator rows from the stage, wait
+//               for mdone, add the TMEM tile and store (or, in dot mode, fold
+//               it into the gradient row).
+// Tiles k+1 (convert), k (MMA) and k-1 (epilogue) overlap, and the stages
+// keep copies of later tiles in flight.  A few large tensor copies per tile
+// instead of one bulk copy per 512-B row: issuing ~65 row copies per tile
+// from one warp capped a CTA at about one tile per 2.8 us.  Every wait is
+// bounded: a timeout sets a shared abort flag that every role checks, so all
+// roles leave their loops.
+constexpr int GRP = 32;          // accumulator rows staged per tile (r <= 32)
+constexpr int WS_THREADS = 352;  // eleven warps
+constexpr int WS_TMEM_COLS = 64; // two accumulator buffers of 32 columns
 
 __device__ __forceinline__ void mbar_init(uint32_t b, uint32_t n) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n));
@@ -310,69 +322,111 @@ __device__ __forceinline__ bool mbar_wait_abort(uint32_t bar, uint32_t phase, vo
     }
   }
 }
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
+__device__ __forceinline__ void tma_store_rows(const CUtensorMap* map, int c0, int c1, int c2, int c3, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
                : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all_but_one() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// named barrier that also ORs a predicate over the participating threads, so
+// that every thread takes the same abort decision
+__device__ __forceinline__ bool bar_or(int id, int n, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
 
 // ACC: accumulator storage (0 fp32, 1 bf16, 2 bf16 value + bf16 compensation),
 // or 3: dot mode -- the staged rows are the r forward fields ubar (fp32) and
 // the gradient row, and the tile is folded into the gradient at once.
 template <int KP, int ACC>
-struct GCfg {
-  static constexpr uint32_t PROW = (ACC == 0 || ACC == 3) ? TILE_M * 4 : TILE_M * 2;  // bytes of one staged row
-  static constexpr uint32_t PBYTES = GRP * PROW * (ACC == 2 ? 2 : 1) + (ACC == 3 ? PROW : 0);
-  static constexpr uint32_t STAGE = (uint32_t)KP * TILE_M * 4 + PBYTES;  // A rows then accumulator rows
+struct WCfg {
+  static constexpr int NSR = KP == 32 ? 4 : 2;  // snapshot stages
+  static constexpr int NSA = KP == 32 ? 5 : 2;  // accumulator stages
+  static constexpr int NA = KP == 32 ? 2 : 1;   // operand buffers (hi + lo each)
+  static constexpr uint32_t RSTAGE = (uint32_t)KP * TILE_M * 4;
+  static constexpr uint32_t PROW = (ACC == 0 || ACC == 3) ? TILE_M * 4 : TILE_M * 2;  // one staged row
+  static constexpr uint32_t ASTAGE = GRP * PROW * (ACC == 2 ? 2 : 1) + (ACC == 3 ? PROW : 0);
   static constexpr uint32_t ABYTES = TILE_M * KP * 4;
   static constexpr uint32_t BBYTES = GRP * KP * 4;
-  static constexpr size_t SMEM = (size_t)GNS * STAGE + 2 * ABYTES + 2 * BBYTES + 8 * (2 * GNS + 1) + 32;
+  // barriers: full_r, empty_r [NSR]; full_a, empty_a [NSA]; aready [NA]; mdone, tfree [2]
+  static constexpr int NBAR = 2 * NSR + 2 * NSA + NA + 4;
+  static constexpr size_t SMEM =
+      (size_t)NSR * RSTAGE + (size_t)NSA * ASTAGE + (size_t)NA * 2 * ABYTES + 2 * BBYTES + 8 * NBAR + 16;
 };
 
+// mR1 / mR2: the ring (all shots' slots as one field family) with boxes of
+// n1 and nlev - n1 rows, the window's slots before and after the ring wraps;
+// mA: the accumulator family (box: the rows of one shot); mG: the gradient
+// family of the dot mode (box: one row).
 template <int KP, int ACC>
-__global__ void __launch_bounds__(GTHREADS)
-probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
-  using C = GCfg<KP, ACC>;
+__global__ void __launch_bounds__(WS_THREADS, 1)
+probe_gemm_ws(const __grid_constant__ CUtensorMap mR1, const __grid_constant__ CUtensorMap mR2,
+              const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mG, GemmArgs a, int NP,
+              long long ntiles, int n1) {
+  using C = WCfg<KP, ACC>;
+  constexpr int NSR = C::NSR, NSA = C::NSA, NA = C::NA;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* stage0 = smem;
-  unsigned char* A_hi = smem + GNS * C::STAGE;
-  unsigned char* A_lo = A_hi + C::ABYTES;
-  unsigned char* B_hi = A_lo + C::ABYTES;
+  unsigned char* rstage0 = smem;
+  unsigned char* astage0 = rstage0 + NSR * C::RSTAGE;
+  unsigned char* A0 = astage0 + NSA * C::ASTAGE;  // operand buffer j: hi at A0 + 2j*ABYTES, lo after it
+  unsigned char* B_hi = A0 + NA * 2 * C::ABYTES;
   unsigned char* B_lo = B_hi + C::BBYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(B_lo + C::BBYTES);
-  const uint32_t full = smem_u32(bars), empty = full + 8 * GNS, mma_bar = empty + 8 * GNS;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * GNS + 1);
+  const uint32_t full_r = smem_u32(bars), empty_r = full_r + 8 * NSR;
+  const uint32_t full_a = empty_r + 8 * NSR, empty_a = full_a + 8 * NSA;
+  const uint32_t aready = empty_a + 8 * NSA, mdone = aready + 8 * NA, tfree = mdone + 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + C::NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int shot = blockIdx.y;
-  const float* ring = a.ring + shot * a.ring_ss;
-  const float* Q = a.Q + shot * a.q_ss;
-  float* Pf = static_cast<float*>(a.P) + shot * a.p_ss;                  // ACC == 0
-  __nv_bfloat16* Ph = static_cast<__nv_bfloat16*>(a.P) + shot * a.p_ss;  // ACC != 0
   const int nxt = (a.L.nx + TILE_M - 1) / TILE_M;
   auto tile_base = [&](long long tile) -> long long {
     const long long row = tile / nxt;
     return a.L.off(row / a.L.ny, row % a.L.ny, (long long)(tile % nxt) * TILE_M);
   };
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(32));
+                 "r"(WS_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < GNS; ++s) {
-      mbar_init(full + 8 * s, 1);
-      mbar_init(empty + 8 * s, GW);
+    for (int s = 0; s < NSR; ++s) {
+      mbar_init(full_r + 8 * s, 1);
+      mbar_init(empty_r + 8 * s, TILE_M);
     }
-    mbar_init(mma_bar, 1);
+    for (int s = 0; s < NSA; ++s) {
+      mbar_init(full_a + 8 * s, 1);
+      mbar_init(empty_a + 8 * s, ACC == 3 ? TILE_M : 1);
+    }
+    for (int j = 0; j < NA; ++j) mbar_init(aready + 8 * j, TILE_M);
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(mdone + 8 * j, 1);
+      mbar_init(tfree + 8 * j, ACC == 3 ? TILE_M : 1);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // B operand (probe block) once per CTA, as in probe_gemm_tf32
-  for (int e = tid; e < NP * KP; e += GTHREADS) {
+  // B operand (the window's probe block, shared by every tile), tf32 hi/lo
+  const float* Q = a.Q + shot * a.q_ss;
+  for (int e = tid; e < NP * KP; e += WS_THREADS) {
     const int n = e / KP, k = e % KP;
     const int row = a.level0 + k + a.qshift;
     float v = 0.f;
@@ -386,179 +440,247 @@ probe_gemm_tma(GemmArgs a, int NP, long long ntiles) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int slot0 = a.level0 % a.nslots;
 
-  if (warp == GW) {
-    // ------------------------------------------------------------ producer warp
-    const int ncp = ACC == 2 ? 2 * a.r : (ACC == 3 ? a.r + 1 : a.r);  // accumulator rows copied per tile
-    const uint32_t bytes = (uint32_t)a.nlev * TILE_M * 4 + (uint32_t)ncp * C::PROW;
+  const int cy = a.L.ndim == 3 ? H : 0;
+  if (warp == 0 || warp == 10) {
+    // ------------------------------------------------------------ producers (lane 0 issues):
+    // warp 0 the snapshot rows, warp 10 the accumulator rows (and the gradient row)
+    const bool snap = warp == 0;
+    const int NS = snap ? NSR : NSA;
+    const uint32_t full = snap ? full_r : full_a, empty = snap ? empty_r : empty_a;
+    const int slot0 = a.level0 % a.nslots;
+    const int nacc = ACC == 2 ? 2 * a.r : a.r;  // accumulator rows of one shot
+    const uint32_t bytes = snap ? (uint32_t)a.nlev * TILE_M * 4
+                                : (uint32_t)nacc * C::PROW + (ACC == 3 ? C::PROW : 0);
     bool ok = true;
-    uint32_t it = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-      const int s = it % GNS;
-      if (it >= (uint32_t)GNS) {
+    uint32_t k = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+      const long long row = tile / nxt;
+      const int c0 = HX + (int)(tile % nxt) * TILE_M, c1 = (int)(row % a.L.ny) + cy, c2 = (int)(row / a.L.ny) + H;
+      const int st = k % NS;
+      if (k >= (uint32_t)NS) {
         bool w = true;
-        if (lane == 0) w = mbar_wait_abort(empty + 8 * s, ((it / GNS) - 1) & 1, abort_flag);
+        if (lane == 0) w = mbar_wait_abort(empty + 8 * st, ((k / NS) - 1) & 1, abort_flag);
         if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) { ok = false; break; }
       }
-      if (lane == 0) mbar_expect_tx(full + 8 * s, bytes);
-      __syncwarp();
-      const long long base = tile_base(tile);
-      const uint32_t dst = smem_u32(stage0 + s * C::STAGE);
-      const uint32_t pdst = dst + (uint32_t)KP * TILE_M * 4;
-      for (int c = lane; c < a.nlev + ncp; c += 32) {
-        if (c < a.nlev) {
-          const int sl = slot0 + c >= a.nslots ? slot0 + c - a.nslots : slot0 + c;
-          bulk_g2s(dst + (uint32_t)c * TILE_M * 4, ring + (long long)sl * a.slot_stride + base, TILE_M * 4, full + 8 * s);
+      if (lane == 0) {
+        mbar_expect_tx(full + 8 * st, bytes);
+        if (snap) {
+          const uint32_t dst = smem_u32(rstage0 + st * C::RSTAGE);
+          tma_rows(dst, &mR1, c0, c1, c2, shot * a.nslots + slot0, full + 8 * st);
+          if (n1 < a.nlev) tma_rows(dst + (uint32_t)n1 * TILE_M * 4, &mR2, c0, c1, c2, shot * a.nslots, full + 8 * st);
         } else {
-          const int idx = c - a.nlev;
-          if (ACC == 3 && idx == a.r) {  // the gradient row, staged after GRP field rows
-            bulk_g2s(pdst + (uint32_t)GRP * C::PROW, a.G + shot * a.g_ss + base, C::PROW, full + 8 * s);
-          } else if (ACC == 0 || ACC == 3) {
-            bulk_g2s(pdst + (uint32_t)idx * C::PROW, Pf + (long long)idx * a.pstride + base, C::PROW, full + 8 * s);
-          } else if (ACC == 1 || idx < a.r) {  // bf16 values
-            bulk_g2s(pdst + (uint32_t)idx * C::PROW, Ph + (long long)idx * a.pstride + base, C::PROW, full + 8 * s);
-          } else {                              // bf16 compensations, staged after GRP value rows
-            const int i = idx - a.r;
-            bulk_g2s(pdst + (uint32_t)(GRP + i) * C::PROW, Ph + (long long)(a.r + i) * a.pstride + base, C::PROW,
-                     full + 8 * s);
-          }
+          const uint32_t dst = smem_u32(astage0 + st * C::ASTAGE);
+          tma_rows(dst, &mA, c0, c1, c2, shot * nacc, full + 8 * st);
+          if (ACC == 3) tma_rows(dst + (uint32_t)GRP * C::PROW, &mG, c0, c1, c2, shot, full + 8 * st);
         }
       }
+      __syncwarp();
     }
     if (!ok && lane == 0) atomicOr(a.err, 1);
-    // drain: every issued stage must have landed before the CTA exits
+    // every issued copy must have landed before the CTA exits (bounded waits)
     if (lane == 0) {
-      for (uint32_t j = (it > (uint32_t)GNS ? it - GNS : 0); j < it; ++j) {
+      for (uint32_t j = (k > (uint32_t)NS ? k - NS : 0); j < k; ++j) {
         const long long t0 = clock64();
-        while (!mbar_wait_abort(full + 8 * (j % GNS), (j / GNS) & 1, abort_flag) && clock64() - t0 < WAIT_CYCLES) {}
+        while (!mbar_wait_abort(full + 8 * (j % NS), (j / NS) & 1, abort_flag) && clock64() - t0 < WAIT_CYCLES) {}
       }
     }
-  } else {
-    // ------------------------------------------------------------ workers
-    const uint32_t idesc = idesc_tf32(TILE_M, NP);
-    const uint32_t sbo = KP * 32, lbo = 128;
-    const uint32_t a_hi_u = smem_u32(A_hi), a_lo_u = smem_u32(A_lo);
-    const uint32_t b_hi_u = smem_u32(B_hi), b_lo_u = smem_u32(B_lo);
-    uint32_t it = 0, mph = 0;
-    bool ok = true;
-    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-      const int s = it % GNS;
-      if (!mbar_wait_abort(full + 8 * s, (it / GNS) & 1, abort_flag)) { ok = false; }
-      bar_named(1, GW * 32);
-      if (*abort_flag) { ok = false; break; }
-      const float* sA = reinterpret_cast<const float*>(stage0 + s * C::STAGE);
-      const float* sP = sA + KP * TILE_M;
-      const __nv_bfloat16* sPh = reinterpret_cast<const __nv_bfloat16*>(sP);
-      // 1. split this thread's point column of the staged snapshots
-#pragma unroll
-      for (int k4 = 0; k4 < KP; k4 += 4) {
-        float v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = (k4 + j < a.nlev) ? sA[(k4 + j) * TILE_M + tid] : 0.f;
-        float4 hi, lo;
-        hi.x = tf32_hi(v[0]); hi.y = tf32_hi(v[1]); hi.z = tf32_hi(v[2]); hi.w = tf32_hi(v[3]);
-        lo.x = v[0] - hi.x; lo.y = v[1] - hi.y; lo.z = v[2] - hi.z; lo.w = v[3] - hi.w;
-        const uint32_t o = kmaj_off(tid, k4, KP);
-        *reinterpret_cast<float4*>(A_hi + o) = hi;
-        *reinterpret_cast<float4*>(A_lo + o) = lo;
-      }
-      // 2. old accumulators of this point, then release the stage
-      float pold[GRP];  // old accumulators, or the forward fields in dot mode
-#pragma unroll
-      for (int i = 0; i < GRP; ++i) {
-        float v = 0.f;
-        if (i < a.r) {
-          if (ACC == 0 || ACC == 3) v = sP[i * TILE_M + tid];
-          else v = __bfloat162float(sPh[i * TILE_M + tid]);
-          if (ACC == 2) v += __bfloat162float(sPh[(GRP + i) * TILE_M + tid]);
-        }
-        pold[i] = v;
-      }
-      const float gold = ACC == 3 ? sP[GRP * TILE_M + tid] : 0.f;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(empty + 8 * s);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      bar_named(1, GW * 32);
-      // 3. MMAs
-      if (tid == 0) {
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(TILE_M, NP);
+      const uint32_t sbo = KP * 32, lbo = 128;
+      const uint32_t b_hi_u = smem_u32(B_hi), b_lo_u = smem_u32(B_lo);
+      bool ok = true;
+      long long issued = -1;
+      uint32_t k = 0;
+      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int ja = k % NA, jt = k & 1;
+        if (!mbar_wait_abort(aready + 8 * ja, (k / NA) & 1, abort_flag)) { ok = false; break; }
+        if (k >= 2 && !mbar_wait_abort(tfree + 8 * jt, ((k - 2) / 2) & 1, abort_flag)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_hi_u = smem_u32(A0 + 2 * ja * C::ABYTES), a_lo_u = a_hi_u + C::ABYTES;
+        const uint32_t d = tmem + (uint32_t)(jt * 32);
 #pragma unroll
         for (int kk = 0; kk < KP / 8; ++kk) {
           const uint32_t ko = kk * 2 * 128;
           const uint64_t ah = smem_desc(a_hi_u + ko, lbo, sbo), al = smem_desc(a_lo_u + ko, lbo, sbo);
           const uint64_t bh = smem_desc(b_hi_u + ko, lbo, sbo), bl = smem_desc(b_lo_u + ko, lbo, sbo);
-          mma_tf32(tmem, ah, bh, idesc, kk > 0 ? 1u : 0u);
-          mma_tf32(tmem, al, bh, idesc, 1u);
-          if (a.q_has_lo) mma_tf32(tmem, ah, bl, idesc, 1u);
+          mma_tf32(d, ah, bh, idesc, kk > 0 ? 1u : 0u);
+          mma_tf32(d, al, bh, idesc, 1u);
+          if (a.q_has_lo) mma_tf32(d, ah, bl, idesc, 1u);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mma_bar)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mdone + 8 * jt)
                      : "memory");
+        issued = k;
       }
-      // 4. epilogue
-      int done = 1;
-      if (tid == 0) done = mbar_wait_abort(mma_bar, mph, abort_flag) ? 1 : 0;
-      mph ^= 1u;
-      bar_named(1, GW * 32);
-      if (*abort_flag || !done) { ok = false; break; }
+      if (!ok) {
+        atomicOr(a.err, 1);
+        // let the MMAs already issued finish before TMEM is released (bounded)
+        if (issued >= 0) {
+          const uint32_t kl = (uint32_t)issued;
+          mbar_wait(mdone + 8 * (kl & 1), (kl / 2) & 1);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp < 6) {
+    // ------------------------------------------------------------ converters: one point per thread
+    const int m = tid - 64;
+    bool ok = true;
+    uint32_t k = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+      const int sr = k % NSR, ja = k % NA;
+      if (!mbar_wait_abort(full_r + 8 * sr, (k / NSR) & 1, abort_flag)) { ok = false; break; }
+      if (k >= (uint32_t)NA) {  // the MMAs of tile k - NA have finished reading operand buffer ja
+        const uint32_t kp = k - NA;
+        if (!mbar_wait_abort(mdone + 8 * (kp & 1), (kp / 2) & 1, abort_flag)) { ok = false; break; }
+      }
+      const float* sA = reinterpret_cast<const float*>(rstage0 + sr * C::RSTAGE);
+      unsigned char* A_hi = A0 + 2 * ja * C::ABYTES;
+      unsigned char* A_lo = A_hi + C::ABYTES;
+#pragma unroll
+      for (int k4 = 0; k4 < KP; k4 += 4) {
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = (k4 + j < a.nlev) ? sA[(k4 + j) * TILE_M + m] : 0.f;
+        float4 hi, lo;
+        hi.x = tf32_hi(v[0]); hi.y = tf32_hi(v[1]); hi.z = tf32_hi(v[2]); hi.w = tf32_hi(v[3]);
+        lo.x = v[0] - hi.x; lo.y = v[1] - hi.y; lo.z = v[2] - hi.z; lo.w = v[3] - hi.w;
+        const uint32_t o = kmaj_off(m, k4, KP);
+        *reinterpret_cast<float4*>(A_hi + o) = hi;
+        *reinterpret_cast<float4*>(A_lo + o) = lo;
+      }
+      mbar_arrive(empty_r + 8 * sr);  // this thread's reads of the snapshot stage are done
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(aready + 8 * ja);
+    }
+    if (!ok && m == 0) atomicOr(a.err, 1);
+  } else {
+    // ------------------------------------------------------------ epilogue: TMEM lane quadrant warp % 4
+    // The new accumulator values overwrite the staged old ones in shared
+    // memory, and one TMA tensor store per tile writes them back; the stage
+    // is released once that store has read it (one tile later).
+    const int q = warp & 3, m = q * 32 + lane, et = tid - 192;
+    bool ok = true;
+    uint32_t k = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+      const int sa = k % NSA, jt = k & 1;
+      if (ACC == 3) {
+        // dot mode: the staged rows are only read, so the stage is released
+        // as soon as every thread holds its point's values; the gradient row
+        // goes back with one plain store per thread
+        if (!mbar_wait_abort(full_a + 8 * sa, (k / NSA) & 1, abort_flag)) { ok = false; break; }
+        const float* sP = reinterpret_cast<const float*>(astage0 + sa * C::ASTAGE);
+        float ub[GRP];
+#pragma unroll
+        for (int i = 0; i < GRP; ++i) ub[i] = i < a.r ? sP[i * TILE_M + m] : 0.f;
+        const float gold = sP[GRP * TILE_M + m];
+        mbar_arrive(empty_a + 8 * sa);
+        if (!mbar_wait_abort(mdone + 8 * jt, (k / 2) & 1, abort_flag)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * 32);
+        float dot = 0.f;
+#pragma unroll
+        for (int c = 0; c < GRP / 16; ++c) {
+          if (c * 16 < NP) {
+            float acc[16];
+            tmem_ld16(trow + (uint32_t)(c * 16), acc);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c * 16 + j < a.r) dot = fmaf(ub[c * 16 + j], acc[j], dot);
+          }
+        }
+        a.G[shot * a.g_ss + tile_base(tile) + m] = gold + dot;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(tfree + 8 * jt);
+        continue;
+      }
+      // each thread waits for itself; the barrier before the store takes the
+      // abort decision for all of them at once
+      bool w = mbar_wait_abort(full_a + 8 * sa, (k / NSA) & 1, abort_flag);
+      if (w) w = mbar_wait_abort(mdone + 8 * jt, (k / 2) & 1, abort_flag);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const long long prow = tile_base(tile) + tid;
-      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-      float dot = 0.f;
+      float* sP = reinterpret_cast<float*>(astage0 + sa * C::ASTAGE);
+      __nv_bfloat16* sPh = reinterpret_cast<__nv_bfloat16*>(sP);
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(jt * 32);
 #pragma unroll
       for (int c = 0; c < GRP / 16; ++c) {
-        if (c * 16 < NP) {
+        if (w && c * 16 < NP) {
           float acc[16];
           tmem_ld16(trow + (uint32_t)(c * 16), acc);
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int i = c * 16 + j;
-            if (ACC == 3) {
-              if (i < a.r) dot = fmaf(pold[i], acc[j], dot);
-            } else if (i < a.r) {
-              const float nv = pold[i] + acc[j];
+            if (i < a.r) {
               if (ACC == 0) {
-                Pf[(long long)i * a.pstride + prow] = nv;
+                sP[i * TILE_M + m] += acc[j];
               } else {
+                float old = __bfloat162float(sPh[i * TILE_M + m]);
+                if (ACC == 2) old += __bfloat162float(sPh[(a.r + i) * TILE_M + m]);  // compensations follow the values
+                const float nv = old + acc[j];
                 const __nv_bfloat16 hv = __float2bfloat16_rn(nv);
-                Ph[(long long)i * a.pstride + prow] = hv;
+                sPh[i * TILE_M + m] = hv;
                 // compensation: the rounding error of the stored value
-                if (ACC == 2) Ph[(long long)(a.r + i) * a.pstride + prow] = __float2bfloat16_rn(nv - __bfloat162float(hv));
+                if (ACC == 2) sPh[(a.r + i) * TILE_M + m] = __float2bfloat16_rn(nv - __bfloat162float(hv));
               }
             }
           }
         }
       }
-      if (ACC == 3) a.G[shot * a.g_ss + prow] = gold + dot;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      // the tile's new values are in the stage and its TMEM columns are read
+      if (bar_or(2, TILE_M, !w)) { ok = false; break; }
+      if (et == 0) {
+        mbar_arrive(tfree + 8 * jt);
+        const long long row = tile / nxt;
+        const int c0 = HX + (int)(tile % nxt) * TILE_M, c1 = (int)(row % a.L.ny) + cy, c2 = (int)(row / a.L.ny) + H;
+        tma_store_rows(&mA, c0, c1, c2, shot * (ACC == 2 ? 2 * a.r : a.r), smem_u32(sP));
+        bulk_wait_read_all_but_one();  // the previous tile's store has read its stage
+        if (k >= 1) mbar_arrive(empty_a + 8 * ((k - 1) % NSA));
+      }
     }
-    if (!ok && tid == 0) atomicOr(a.err, 1);
+    if (et == 0) {
+      bulk_wait_all();
+      if (!ok) atomicOr(a.err, 1);
+    }
   }
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WS_TMEM_COLS));
   }
 }
 
 template <int KP, int ACC>
-cudaError_t launch_tma(const GemmArgs& a, cudaStream_t s) {
-  using C = GCfg<KP, ACC>;
+cudaError_t launch_ws(const GemmArgs& a, cudaStream_t s) {
+  using C = WCfg<KP, ACC>;
+  static_assert(C::SMEM <= 227 * 1024, "shared memory of the pipelined GEMM");
   const int NP = std::max(16, (a.r + 15) / 16 * 16);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(probe_gemm_tma<KP, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaFuncSetAttribute(probe_gemm_ws<KP, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     attr = true;
   }
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int occ = std::max(1, std::min(4, (int)((228 * 1024) / (C::SMEM + 1024))));
   const long long ntiles = (long long)a.L.nz * a.L.ny * ((a.L.nx + TILE_M - 1) / TILE_M);
-  const long long grid_x = std::min<long long>(ntiles, (long long)sms * occ);
+  const long long grid_x = std::min<long long>(ntiles, (long long)sms);  // one CTA per SM
   dim3 grid((unsigned)grid_x, a.nshots);
-  probe_gemm_tma<KP, ACC><<<grid, GTHREADS, C::SMEM, s>>>(a, NP, ntiles);
+  // the window's slots, split where the ring wraps
+  const int slot0 = a.level0 % a.nslots;
+  const int n1 = std::min(a.nlev, a.nslots - slot0), n2 = a.nlev - n1;
+  const int esize = (ACC == 1 || ACC == 2) ? 2 : 4;
+  const int nacc = ACC == 2 ? 2 * a.r : a.r;
+  CUtensorMap mR1, mR2, mA, mG;
+  if (!encode_field_map(a.L, a.ring, (long long)a.nshots * a.nslots, 4, TILE_M, 1, n1, &mR1) ||
+      !encode_field_map(a.L, a.ring, (long long)a.nshots * a.nslots, 4, TILE_M, 1, n2 > 0 ? n2 : 1, &mR2) ||
+      !encode_field_map(a.L, a.P, (long long)a.nshots * nacc, esize, TILE_M, 1, nacc, &mA) ||
+      !encode_field_map(a.L, ACC == 3 ? (const void*)a.G : a.P, a.nshots, 4, TILE_M, 1, 1, &mG))
+    return cudaErrorInvalidValue;
+  probe_gemm_ws<KP, ACC><<<grid, WS_THREADS, C::SMEM, s>>>(mR1, mR2, mA, mG, a, NP, ntiles, n1);
   return cudaGetLastError();
 }
 
@@ -603,11 +725,11 @@ cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
   cudaError_t e;
   if (a.acc != 0 || (a.r <= GRP && variant == 0)) {  // bf16 storage and dot mode exist on this path only (r <= 32)
     if (a.nlev <= 32)
-      e = a.acc == 0 ? launch_tma<32, 0>(a, s)
-                     : (a.acc == 1 ? launch_tma<32, 1>(a, s) : (a.acc == 2 ? launch_tma<32, 2>(a, s) : launch_tma<32, 3>(a, s)));
+      e = a.acc == 0 ? launch_ws<32, 0>(a, s)
+                     : (a.acc == 1 ? launch_ws<32, 1>(a, s) : (a.acc == 2 ? launch_ws<32, 2>(a, s) : launch_ws<32, 3>(a, s)));
     else
-      e = a.acc == 0 ? launch_tma<64, 0>(a, s)
-                     : (a.acc == 1 ? launch_tma<64, 1>(a, s) : (a.acc == 2 ? launch_tma<64, 2>(a, s) : launch_tma<64, 3>(a, s)));
+      e = a.acc == 0 ? launch_ws<64, 0>(a, s)
+                     : (a.acc == 1 ? launch_ws<64, 1>(a, s) : (a.acc == 2 ? launch_ws<64, 2>(a, s) : launch_ws<64, 3>(a, s)));
   } else if (a.nlev <= 32) {
     e = a.r <= 16 ? launch_kp<32, 16>(a, s) : (a.r <= 32 ? launch_kp<32, 32>(a, s) : launch_kp<32, 0>(a, s));
   } else {

@@ -2,6 +2,7 @@
 // Not part of the public ABI (see include/tprobe.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -82,6 +83,11 @@ struct StencilArgs {
 };
 cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& a,
                            cudaStream_t s, int* err);
+// 4-D TMA map over a family of `nfields` consecutive padded fields of `esize`
+// bytes per value (4: fp32, 2: bf16): dims (px, py, pz, nfields), box
+// (box_x, box_y, 1, box_fields), no swizzle; encoded once per distinct key.
+bool encode_field_map(const Layout& L, const void* base, long long nfields, int esize, int box_x, int box_y,
+                      int box_fields, CUtensorMap* out);
 
 // ---------------------------------------------------------------- probe GEMM
 // P[s][i][x] += sum_{k < nlev} ring[s][(level0 + k) mod nslots][x] * Q[s][level0 + k + qshift][i]

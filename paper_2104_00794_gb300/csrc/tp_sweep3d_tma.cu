@@ -338,20 +338,29 @@ EncodeFn encode_fn() {
 
 struct MapKey {
   const void* base;
-  int nfields, bw, bh;
+  long long nfields;
+  int esize, b0, b1, b3;
   long long field;
   int px, py, pz;
   bool operator==(const MapKey& o) const {
-    return base == o.base && nfields == o.nfields && bw == o.bw && bh == o.bh && field == o.field && px == o.px &&
-           py == o.py && pz == o.pz;
+    return base == o.base && nfields == o.nfields && esize == o.esize && b0 == o.b0 && b1 == o.b1 && b3 == o.b3 &&
+           field == o.field && px == o.px && py == o.py && pz == o.pz;
   }
 };
 
-// Small cache of encoded maps (the buffers of one call are few and stable).
 bool get_map(const Layout& L, const FieldRef& f, int bw, int bh, CUtensorMap* out) {
+  return encode_field_map(L, f.base, f.nfields, 4, bw, bh, 1, out);
+}
+
+}  // namespace
+
+// 4-D map over a family of padded fields, dims (px, py, pz, nfields), with a
+// small cache of encoded maps (the buffers of one call are few and stable).
+bool encode_field_map(const Layout& L, const void* base, long long nfields, int esize, int box_x, int box_y,
+                      int box_fields, CUtensorMap* out) {
   static std::mutex m;
   static std::vector<std::pair<MapKey, CUtensorMap>> cache;
-  const MapKey key{f.base, f.nfields, bw, bh, L.field, L.px, L.py, L.pz};
+  const MapKey key{base, nfields, esize, box_x, box_y, box_fields, L.field, L.px, L.py, L.pz};
   std::lock_guard<std::mutex> lk(m);
   for (auto& e : cache)
     if (e.first == key) {
@@ -361,19 +370,22 @@ bool get_map(const Layout& L, const FieldRef& f, int bw, int bh, CUtensorMap* ou
   EncodeFn enc = encode_fn();
   if (!enc) return false;
   CUtensorMap map;
-  const cuuint64_t dims[4] = {(cuuint64_t)L.px, (cuuint64_t)L.py, (cuuint64_t)L.pz, (cuuint64_t)f.nfields};
-  const cuuint64_t strides[3] = {(cuuint64_t)L.px * 4, (cuuint64_t)L.plane * 4, (cuuint64_t)L.field * 4};
-  const cuuint32_t box[4] = {(cuuint32_t)bw, (cuuint32_t)bh, 1, 1};
+  const cuuint64_t es = (cuuint64_t)esize;
+  const cuuint64_t dims[4] = {(cuuint64_t)L.px, (cuuint64_t)L.py, (cuuint64_t)L.pz, (cuuint64_t)nfields};
+  const cuuint64_t strides[3] = {(cuuint64_t)L.px * es, (cuuint64_t)L.plane * es, (cuuint64_t)L.field * es};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, (cuuint32_t)box_fields};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(f.base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(&map, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return false;
   if (cache.size() >= 64) cache.erase(cache.begin());
   cache.emplace_back(key, map);
   *out = map;
   return true;
 }
+
+namespace {
 
 template <int R, int MODE, class C>
 cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
