@@ -369,7 +369,8 @@ def main():
     avg_stencil_ms = st["ms"] / max(st["launches"], 1)
     stencil_bytes = STENCIL_BYTES_PER_POINT * w.N * w.nshots
     achieved = stencil_bytes / (avg_stencil_ms * 1e-3) / 1e9
-    traffic = profile_traffic("stencil_step_3d_256cubed.md", "paper_2104_00794_gb300/csrc/tp_stencil.cu")
+    traffic = profile_traffic("stencil_step_3d_256cubed.md", "paper_2104_00794_gb300/csrc/tp_sweep3d_tma.cu")
+    gemm_traffic = profile_traffic("probe_gemm_3d_256cubed.md", "paper_2104_00794_gb300/csrc/tp_gemm.cu")
     gm = kern["probe_gemm_tcgen05"]
     avg_gemm_ms = gm["ms"] / max(gm["launches"], 1)
     # algorithmic bytes of one window GEMM: T snapshots read + r accumulators read and written
@@ -484,7 +485,11 @@ def main():
                          "traffic": traffic, "bytes_per_launch_algorithmic": stencil_bytes,
                          "avg_launch_ms": avg_stencil_ms, "launches": st["launches"]},
             "probe_gemm": {"avg_launch_ms": avg_gemm_ms, "launches": gm["launches"],
+                           "bytes_per_launch_algorithmic": gemm_bytes,
                            "achieved_gbs": gemm_bytes / (avg_gemm_ms * 1e-3) / 1e9 if gm["launches"] else None,
+                           "frac_of_hbm": (gemm_bytes / (avg_gemm_ms * 1e-3) / 1e9 / hbm_peak
+                                           if gm["launches"] and hbm_peak else None),
+                           "traffic": gemm_traffic,
                            "tensor_tflops": gemm_flops / (avg_gemm_ms * 1e-3) / 1e12 if gm["launches"] else None},
             "kernels": {k: v for k, v in kern.items() if v["launches"]},
             "gpu_launches": launches,

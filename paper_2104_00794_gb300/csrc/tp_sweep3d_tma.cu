@@ -257,18 +257,32 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
       // w_0 * 3u + sum_k w_k (neighbours) for exact weights, but annihilates constants
       // whatever the fp32 rounding of the weights (the plain sum form leaves a spurious
       // zero-order term that makes long runs drift).
-      float s4[4] = {0.f, 0.f, 0.f, 0.f};
+      // Two points per instruction with the packed fp32x2 FMA / ADD: each lane
+      // is the IEEE round-to-nearest operation of the scalar form, in the same
+      // order (u[+k] - u as fma(u, -1, u[+k]), exact product), so the result is
+      // bit-identical to the scalar loop at half the instruction count.
+      float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
       for (int k = 1; k <= R; ++k) {
         const float4 yp = Uc[cidx + k * RW], ym = Uc[cidx - k * RW];
+        const float4 zp = q[R + k], zm = q[R - k];
+        const float2 wk = make_float2(a.W.w[k], a.W.w[k]);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const float c = v[4 + p];
-          const float t = ((v[4 + p + k] - c) + (v[4 + p - k] - c)) + ((comp(yp, p) - c) + (comp(ym, p) - c)) +
-                          ((comp(q[R + k], p) - c) + (comp(q[R - k], p) - c));
-          s4[p] = fmaf(a.W.w[k], t, s4[p]);
+        for (int h = 0; h < 2; ++h) {
+          const int p = 2 * h;
+          const float2 c = make_float2(v[4 + p], v[5 + p]);
+          const float2 dxp = __ffma2_rn(c, neg1, make_float2(v[4 + p + k], v[5 + p + k]));
+          const float2 dxm = __ffma2_rn(c, neg1, make_float2(v[4 + p - k], v[5 + p - k]));
+          const float2 dyp = __ffma2_rn(c, neg1, h ? make_float2(yp.z, yp.w) : make_float2(yp.x, yp.y));
+          const float2 dym = __ffma2_rn(c, neg1, h ? make_float2(ym.z, ym.w) : make_float2(ym.x, ym.y));
+          const float2 dzp = __ffma2_rn(c, neg1, h ? make_float2(zp.z, zp.w) : make_float2(zp.x, zp.y));
+          const float2 dzm = __ffma2_rn(c, neg1, h ? make_float2(zm.z, zm.w) : make_float2(zm.x, zm.y));
+          const float2 t = __fadd2_rn(__fadd2_rn(__fadd2_rn(dxp, dxm), __fadd2_rn(dyp, dym)), __fadd2_rn(dzp, dzm));
+          s2[h] = __ffma2_rn(wk, t, s2[h]);
         }
       }
+      const float s4[4] = {s2[0].x, s2[0].y, s2[1].x, s2[1].y};
       const float4 c1 = reinterpret_cast<const float4*>(sP1 + sp * C::PFL)[ty * (BX / 4) + tx];
       const float4 c2 = reinterpret_cast<const float4*>(sP2 + sp * C::PFL)[ty * (BX / 4) + tx];
       float res[4], inc[4];
@@ -415,9 +429,21 @@ cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cu
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // as many z chunks per tile column as keep one wave of 2 CTAs per SM busy
-  const long long cols = (long long)t.ntx * t.nty * a.nshots, slots = 2LL * sms;
+  // z chunks per tile column: the fewest that fill the CTA slots (2 per SM)
+  // to at least 90 % over whole waves, else as many as keep one wave busy
+  // (256^3: 64 columns x 9 chunks on 304 slots ran 3 % faster than 4 chunks,
+  // which left 48 slots idle)
+  const int occ = (int)std::max<size_t>(1, std::min<size_t>(2, (228 * 1024) / (C::SMEM + 1024)));
+  const long long cols = (long long)t.ntx * t.nty * a.nshots, slots = (long long)occ * sms;
+  const int zmax = std::max(1, L.nz / (3 * R));
   t.nzc = (int)std::max<long long>(1, std::min<long long>(slots / cols, std::max(1, L.nz / (4 * R))));
+  for (int c = (int)std::max<long long>(1, (slots + cols - 1) / cols); c <= zmax; ++c) {
+    const long long items = cols * c, waves = (items + slots - 1) / slots;
+    if (items * 10 >= waves * slots * 9 && waves <= 3) {
+      t.nzc = c;
+      break;
+    }
+  }
   t.zchunk = (L.nz + t.nzc - 1) / t.nzc;
   t.nzc = (L.nz + t.zchunk - 1) / t.zchunk;
   t.items = cols * t.nzc;
@@ -427,7 +453,9 @@ cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cu
 }
 
 // 64 x 16 tiles, 3 planes of lookahead: 128 x 8, 32 x 32 tiles measured the
-// same on GB300 and 4 planes of lookahead slower (2 CTAs per SM either way).
+// same on GB300, 4 planes the same, and one CTA per SM with 6 or 9 planes of
+// lookahead 20 % slower: the consumers' per-SM throughput, not the depth of
+// the copy pipeline, sets the pace.
 template <int R, int MODE>
 cudaError_t launch_t(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
   return launch_c<R, MODE, Cfg<R, 64, 16, 3>>(L, W, a, s, err);
