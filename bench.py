@@ -269,34 +269,26 @@ def wl_seed():
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2104_00794_gb300.replicas import Replicas
+    reps = Replicas()
+    world, rank, local = reps.world, reps.rank, reps.local
     if args.impl == "reference":
         return run_reference(args, rank)
 
     import torch
-    import torch.distributed as dist
     from paper_2104_00794_gb300 import api, native
     from paper_2104_00794_gb300 import workloads as wl
 
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    reps.init("nccl", torch.device("cuda", local))
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        reps.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = reps.max_over_ranks
 
-    w = make_workload(args, seed_offset=rank)
+    w = make_workload(args, seed_offset=reps.seed_offset())
     p = api.Problem.from_workload(w, form=args.form)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
     vel_true, vel0, wav = dev(w.vel_true), dev(w.vel0), dev(w.wavelet)
@@ -358,7 +350,7 @@ def main():
     clocks = clk.summary()
     p.status(native.OP_GRADIENT_PROBED)
     ms_max = max_over_ranks(ms)
-    value = pts * world / (ms_max * 1e-3) / 1e9
+    value = reps.whole_job_rate(pts, ms_max) / 1e9
     grad_probed = grad.clone()
     mem = api.memory_model(p, probe)
     p.release()
@@ -503,8 +495,7 @@ def main():
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    reps.close()
 
 
 if __name__ == "__main__":
