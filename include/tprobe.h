@@ -191,6 +191,27 @@ tp_status tp_probed_backward(const tp_grid* grid, const tp_geom* geom, const tp_
                              int wrt_velocity, float* grad, double* gnorm, void* state,
                              size_t state_bytes, void* ws, size_t ws_bytes, void* stream);
 
+/* Imaging conditions on the probed wavefields (§Imaging conditions, Eq. 5:
+ * a linear operator D that acts on space only commutes with probing,
+ * Q^T (D u) = D (Q^T u)).  tp_probed_image applies D to the r probed fields
+ * P_i = sum_{j=2}^{nt-2} Q[j+1, i] u[j] (the state of tp_probed_forward) and
+ * V_i = sum_{k=2}^{nt-1} Q[k, i] lambda[k] (an adjoint run driven by adj_src,
+ * [nshots][nt][nrec]) instead of to nt snapshots:
+ *   image(x) = scale * sum_shots sum_i <D P_i(x), D V_i(x)>,
+ * an estimate of sum_shots sum_j <D u[j](x), D lambda[j+1](x)> (exact for
+ * TP_PROBE_IDENTITY).  image: device [nz][ny][nx] fp32.  The probe must use
+ * TP_ACC_F32 storage; ws: tp_workspace_bytes(TP_OP_PROBED_BACKWARD, ...);
+ * the same grid, geom, probe and vel as the forward half.  The state is only
+ * read.  Errors as tp_probed_backward, TP_ERR_ARG for an unknown cond. */
+typedef enum {
+  TP_IMAGE_CORRELATION = 0,  /* D = identity: cross-correlation image */
+  TP_IMAGE_GRADIENT = 1      /* D = spatial gradient (centred first differences of the
+                                grid's order, divided by h), summed over the axes */
+} tp_image_cond;
+tp_status tp_probed_image(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe, const float* vel,
+                          const float* adj_src, int cond, float* image, const void* state, size_t state_bytes,
+                          void* ws, size_t ws_bytes, void* stream);
+
 /* Range-finding probes of Eq. 6 for every shot: Q_s = qr(D_s D_s^T Z_s), where
  * D_s = d_obs[s] is the observed record as an nt x nrec matrix (time x
  * receivers) and Z_s the random probes that `probe` (kind RADEMACHER or

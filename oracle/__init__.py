@@ -18,6 +18,9 @@ the paper it follows in ``tp_oracle.c``:
                    Irwin-Hall Gaussian, identity)
   qr_probes        Eq. 6 range-finding probes qr(D D^T Z) (numpy / LAPACK)
   fd_weights       Fornberg (1988) centred second-derivative weights
+  image_full       imaging conditions applied to every time step (numpy)
+  image_probed     the same conditions applied to the probed fields (Eq. 5)
+  fd_weights_first Fornberg (1988) centred first-derivative weights (numpy)
 """
 from __future__ import annotations
 
@@ -241,3 +244,121 @@ def batch_forward(w, vel, nt=None):
     g = grid_of(w, nt)
     return np.stack([forward(g, w.src[s], w.rec[s], vel, w.wavelet[s][: g.nt])
                      for s in range(w.nshots)])
+
+
+# ------------------------------------------------------------------ imaging conditions
+IMAGE_CONDS = {"correlation": 0, "gradient": 1}
+
+
+def fornberg(m: int, x0: float, xs) -> np.ndarray:
+    """Weights of the m-th derivative at x0 on the nodes xs, by Fornberg's
+    (1988) recursion over the nodes (weights of every order up to m are built
+    together, one node at a time)."""
+    xs = np.asarray(xs, dtype=np.float64)
+    n = xs.size
+    c = np.zeros((n, m + 1))
+    c[0, 0] = 1.0
+    prod_prev = 1.0
+    d_prev = xs[0] - x0
+    for i in range(1, n):
+        kmax = min(i, m)
+        prod = 1.0
+        d_old = d_prev
+        d_prev = xs[i] - x0
+        for j in range(i):
+            diff = xs[i] - xs[j]
+            prod *= diff
+            if j == i - 1:
+                for k in range(kmax, 0, -1):
+                    c[i, k] = prod_prev * (k * c[i - 1, k - 1] - d_old * c[i - 1, k]) / prod
+                c[i, 0] = -prod_prev * d_old * c[i - 1, 0] / prod
+            for k in range(kmax, 0, -1):
+                c[j, k] = (d_prev * c[j, k] - k * c[j, k - 1]) / diff
+            c[j, 0] = d_prev * c[j, 0] / diff
+        prod_prev = prod
+    return c[:, m]
+
+
+def fd_weights_first(order: int) -> np.ndarray:
+    """c_1..c_R of the centred first derivative of order 2R = `order`:
+    f'(x) ~ sum_k c_k (f(x + k h) - f(x - k h)) / h."""
+    R = order // 2
+    w = fornberg(1, 0.0, np.arange(-R, R + 1, dtype=np.float64))
+    return w[R + 1:]
+
+
+def _field(g: Grid, f) -> np.ndarray:
+    f = np.asarray(f, dtype=np.float64)
+    return f.reshape((g.nz, g.ny, g.nx)) if g.ndim == 3 else f.reshape((g.nz, g.nx))
+
+
+def _derivative(g: Grid, f: np.ndarray, axis: int) -> np.ndarray:
+    """Centred first difference of the grid's order along `axis`, with zero
+    values outside the grid (the modelling's Dirichlet boundary)."""
+    c = fd_weights_first(g.order)
+    R = c.size
+    pad = [(0, 0)] * f.ndim
+    pad[axis] = (R, R)
+    fp = np.pad(f, pad)
+    n = f.shape[axis]
+    out = np.zeros_like(f)
+    for k in range(1, R + 1):
+        plus = np.take(fp, np.arange(R + k, R + k + n), axis=axis)
+        minus = np.take(fp, np.arange(R - k, R - k + n), axis=axis)
+        out += c[k - 1] * (plus - minus)
+    return out / g.h
+
+
+def image_of_fields(g: Grid, a, b, cond: str) -> np.ndarray:
+    """<D a, D b> at every grid point: D = identity ("correlation") or the
+    spatial gradient ("gradient", the products summed over the axes)."""
+    A, B = _field(g, a), _field(g, b)
+    if cond == "correlation":
+        return (A * B).ravel()
+    return sum(_derivative(g, A, ax) * _derivative(g, B, ax) for ax in range(A.ndim)).ravel()
+
+
+def image_full(g: Grid, src, rec, vel, q, s, cond: str) -> np.ndarray:
+    """The imaging condition applied at every time step, without probing:
+    sum_{j=2}^{nt-2} <D u[j], D lambda[j+1]>, u the forward wavefield of q,
+    lambda the adjoint wavefield driven by s [nt, nrec]."""
+    _, U = forward(g, src, rec, vel, q, keep_history=True)
+    _, Lam = adjoint(g, src, rec, vel, s, keep_history=True)
+    img = np.zeros(g.nx * g.ny * g.nz)
+    for j in range(2, g.nt - 1):
+        img += image_of_fields(g, U[j], Lam[j + 1], cond)
+    return img
+
+
+def image_probed(g: Grid, src, rec, vel, q, s, Q, scale: float, cond: str) -> np.ndarray:
+    """Eq. 5: the same condition applied to the r probed fields
+    P_i = sum_{j=2}^{nt-2} Q[j+1, i] u[j] and V_i = sum_{k=2}^{nt-1} Q[k, i] lambda[k],
+    image = scale * sum_i <D P_i, D V_i>."""
+    Q = np.asarray(Q, dtype=np.float64)
+    _, U = forward(g, src, rec, vel, q, keep_history=True)
+    _, Lam = adjoint(g, src, rec, vel, s, keep_history=True)
+    nt = g.nt
+    P = Q[3:nt].T @ U[2:nt - 1]   # [r, N]
+    V = Q[2:nt].T @ Lam[2:nt]     # [r, N]
+    img = np.zeros(g.nx * g.ny * g.nz)
+    for i in range(Q.shape[1]):
+        img += image_of_fields(g, P[i], V[i], cond)
+    return scale * img
+
+
+def batch_image(w, vel, s_all, cond, kind=None, r=None, seed=None, probed=True, nt=None):
+    """Sum over the workload's shots of image_probed (per-shot probes drawn
+    with shot index s) or of image_full."""
+    kind = kind or w.probe_kind
+    r = r or w.r
+    seed = w.seed if seed is None else seed
+    g = grid_of(w, nt)
+    total = np.zeros(w.N)
+    for sh in range(w.nshots):
+        q = w.wavelet[sh][: g.nt]
+        if probed:
+            Q = probes(kind, g.nt, r, seed, sh)
+            total += image_probed(g, w.src[sh], w.rec[sh], vel, q, s_all[sh], Q, default_scale(kind, r), cond)
+        else:
+            total += image_full(g, w.src[sh], w.rec[sh], vel, q, s_all[sh], cond)
+    return total

@@ -186,6 +186,20 @@ class Problem:
                                   state.numel(), ws, n, _stream())
         return grad, gnorm
 
+    def probed_image(self, vel, adj_src, probe: ProbeSpec, state: torch.Tensor, cond: str = "gradient",
+                     image=None):
+        """Imaging condition on the probed fields (Eq. 5): scale * sum_i <D P_i, D V_i>
+        with P_i from `state` (probed_forward) and V_i from an adjoint run driven by
+        adj_src; cond "correlation" (D = identity) or "gradient" (D = spatial gradient)."""
+        vel, adj_src = _f32(vel, self.device), _f32(adj_src, self.device)
+        if image is None:
+            image = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        ws, n = self.workspace(native.OP_PROBED_BACKWARD, probe)
+        native.tp_probed_image(self.grid, self.geom, probe.to_c(), _ptr(vel), _ptr(adj_src),
+                               native.IMAGE_CONDS[cond], _ptr(image), state.data_ptr(), state.numel(), ws, n,
+                               _stream())
+        return image
+
     def qr_probes(self, d_obs, r: int, seed: int = 2104, kind: str = "rademacher") -> torch.Tensor:
         """Range-finding probes of Eq. 6, [nshots, nt, r], from the observed
         records; use them as ProbeSpec(kind="user", Z_user=Q, r=r)."""

@@ -582,18 +582,15 @@ tp_status probed_backward_fold(const Ctx& c, const tp_grid* grid, const float* v
   return TP_OK;
 }
 
-tp_status probed_backward_impl(const Ctx& c, const tp_grid* grid, const tp_geom* geom, const float* vel,
-                               const float* wavelet, const float* s, int wrt_velocity, float* grad, double* gnorm,
-                               const float* Q, const void* Pacc) {
+// Algorithm 1 lines 4-7 with the two-set accumulators: the adjoint sweep
+// driven by s (all shots) and vbar_i = sum_{k=2}^{nt-1} Q[k, i] lambda[k]
+// into the workspace's V block.
+tp_status adjoint_probes(const Ctx& c, const float* s, const float* Q) {
   const Plan& P = c.P;
-  if (P.acc == TP_ACC_F32_FOLD)
-    return probed_backward_fold(c, grid, vel, wavelet, s, wrt_velocity, grad, gnorm, Q,
-                                static_cast<float*>(const_cast<void*>(Pacc)));
   const size_t fb = (size_t)P.L.field * sizeof(float);
-  const int nt = P.nt, T = P.T, S = P.S, r = P.r;
+  const int nt = P.nt, T = P.T, S = P.S;
   TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));  // levels nt, nt+1 start at zero
   TRY(cudaMemsetAsync(c.at<char>(P.o_V), 0, (size_t)P.nshots * P.acc_elems * P.acc_esize, c.st));
-  TRY(cudaMemsetAsync(c.at<float>(P.o_gacc), 0, (size_t)P.nshots * fb, c.st));
   const Fam ring{P.o_f, (int)P.nf, S};
   auto level = [S](int t) { return t % S; };
   GemmArgs g = gemm_args(c, const_cast<float*>(Q));
@@ -609,7 +606,20 @@ tp_status probed_backward_impl(const Ctx& c, const tp_grid* grid, const tp_geom*
     }
     return TP_OK;
   };
-  TRYS(adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after));
+  return adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after);
+}
+
+tp_status probed_backward_impl(const Ctx& c, const tp_grid* grid, const tp_geom* geom, const float* vel,
+                               const float* wavelet, const float* s, int wrt_velocity, float* grad, double* gnorm,
+                               const float* Q, const void* Pacc) {
+  const Plan& P = c.P;
+  if (P.acc == TP_ACC_F32_FOLD)
+    return probed_backward_fold(c, grid, vel, wavelet, s, wrt_velocity, grad, gnorm, Q,
+                                static_cast<float*>(const_cast<void*>(Pacc)));
+  const size_t fb = (size_t)P.L.field * sizeof(float);
+  const int nt = P.nt, r = P.r;
+  TRY(cudaMemsetAsync(c.at<float>(P.o_gacc), 0, (size_t)P.nshots * fb, c.st));
+  TRYS(adjoint_probes(c, s, Q));
 
   // combine (Algorithm 1 line 8): ubar = v^2 (L P + S^T qbar), grad = -scale sum_i ubar vbar
   const Fam fG{P.o_gacc, P.nshots, 1};
@@ -712,6 +722,25 @@ tp_status tp_probed_backward(const tp_grid* grid, const tp_geom* geom, const tp_
   const char* st = static_cast<const char*>(state);
   return probed_backward_impl(c, grid, geom, vel, wavelet, adj_src, wrt_velocity, grad, gnorm,
                               reinterpret_cast<const float*>(st + P.s_Q), st + P.s_P);
+}
+
+tp_status tp_probed_image(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe, const float* vel,
+                          const float* adj_src, int cond, float* image, const void* state, size_t state_bytes,
+                          void* ws, size_t ws_bytes, void* stream) {
+  Plan P;
+  TRYS(make_plan(TP_OP_PROBED_BACKWARD, grid, geom, probe, &P));
+  TRYS(check_ws(P, ws, ws_bytes));
+  TRYS(check_state(P, const_cast<void*>(state), state_bytes));
+  if (!adj_src || !image) return fail(TP_ERR_ARG, "adj_src/image is NULL");
+  if (cond != TP_IMAGE_CORRELATION && cond != TP_IMAGE_GRADIENT) return fail(TP_ERR_ARG, "unknown imaging condition %d", cond);
+  if (P.acc != TP_ACC_F32) return fail(TP_ERR_ARG, "imaging conditions need TP_ACC_F32 accumulators");
+  Ctx c{P, static_cast<char*>(ws), static_cast<cudaStream_t>(stream)};
+  TRYS(setup(c, grid, geom, vel));
+  const char* st = static_cast<const char*>(state);
+  TRYS(adjoint_probes(c, adj_src, reinterpret_cast<const float*>(st + P.s_Q)));
+  TRY(launch_image(P.L, grid->order, grid->h, cond, reinterpret_cast<const float*>(st + P.s_P), P.acc_elems,
+                   c.at<float>(P.o_V), P.acc_elems, P.r, P.nshots, P.scale, image, c.st));
+  return TP_OK;
 }
 
 tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float* vel, const float* wavelet,

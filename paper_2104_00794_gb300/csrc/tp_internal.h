@@ -161,6 +161,10 @@ cudaError_t launch_acc_to_f32(const void* P, int acc, int r, int i, long long fi
                               long long out_ss, cudaStream_t s);
 // grad <- grad * (-2 / vel^3): dJ/dv from dJ/dm (m = 1 / v^2)
 cudaError_t launch_chain_velocity(const float* vel, float* grad, long long n, cudaStream_t s);
+// image[x] = scale * sum_s sum_i <D P_s,i, D V_s,i>(x), D per tp_image_cond (tp_image.cu)
+cudaError_t launch_image(const Layout& L, int order, float h, int cond, const float* P, long long p_ss,
+                         const float* V, long long v_ss, int r, int nshots, float scale, float* image,
+                         cudaStream_t s);
 // qbar[s][k][i] = sum_{j=jlo}^{jhi} Q[s][j + qshift][i] * q[s][j][k]
 cudaError_t launch_qbar(const float* Q, int nt, int r, const float* wav, int nsrc, int nshots,
                         int jlo, int jhi, int qshift, float* qbar, cudaStream_t s);

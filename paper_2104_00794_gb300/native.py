@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_ARG", 2: "TP_ERR_UNSTABLE", 3: "TP_ERR_NO
 PROBE_KINDS = {"rademacher": 0, "gaussian": 1, "identity": 2, "user": 3}
 OP_FORWARD, OP_ADJOINT, OP_GRADIENT_PROBED, OP_GRADIENT_FULL, OP_PROBED_FORWARD, OP_PROBED_BACKWARD = range(6)
 ACC_TYPES = {"f32": 0, "bf16": 1, "bf16_kahan": 2, "f32_fold": 3}
+IMAGE_CONDS = {"correlation": 0, "gradient": 1}
 TIME_FORMS = {"levels": 0, "increment": 1}
 KERNEL_KINDS = 6
 
@@ -77,6 +78,7 @@ def lib():
         L.tp_probed_state_bytes.restype = sz
         L.tp_probed_forward.argtypes = [G, E, Pr, vp, vp, vp, vp, sz, vp, sz, vp]
         L.tp_probed_backward.argtypes = [G, E, Pr, vp, vp, vp, i32, vp, vp, vp, sz, vp, sz, vp]
+        L.tp_probed_image.argtypes = [G, E, Pr, vp, vp, i32, vp, vp, sz, vp, sz, vp]
         L.tp_last_error.restype = ctypes.c_char_p
         L.tp_profile_begin.argtypes = [i32]
         L.tp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -84,7 +86,7 @@ def lib():
         L.tp_kernel_name.restype = ctypes.c_char_p
         for f in ("tp_forward", "tp_adjoint", "tp_gradient_probed", "tp_gradient_full", "tp_probes",
                   "tp_workspace_status", "tp_profile_begin", "tp_profile_end", "tp_misfit_noalloc",
-                  "tp_probed_forward", "tp_probed_backward", "tp_qr_probes"):
+                  "tp_probed_forward", "tp_probed_backward", "tp_qr_probes", "tp_probed_image"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
         return L
@@ -150,6 +152,11 @@ def tp_qr_workspace_bytes(nt, nrec, nshots, r) -> int:
     if n == 0:
         raise TprobeError(TP_ERR_ARG, "invalid sizes for range-finding probes")
     return int(n)
+
+
+def tp_probed_image(grid, geom, probe, vel, adj_src, cond, image, state, state_bytes, ws, ws_bytes, stream):
+    _check(lib().tp_probed_image(ctypes.byref(grid), ctypes.byref(geom), ctypes.byref(probe), vel, adj_src,
+                                 int(cond), image, state, state_bytes, ws, ws_bytes, stream))
 
 
 def tp_qr_probes(probe, nt, nrec, nshots, d_obs, Q, ws, ws_bytes, stream):
