@@ -44,7 +44,8 @@ PROBE_KINDS = {"rademacher": 0, "gaussian": 1, "identity": 2}
 class Grid(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("nt", ctypes.c_int), ("order", ctypes.c_int),
-                ("h", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("h", ctypes.c_double), ("dt", ctypes.c_double),
+                ("sponge", ctypes.c_int), ("sponge_eta", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -101,13 +102,17 @@ def _i64(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.int64).ravel())
 
 
-def make_grid(ndim, nx, ny, nz, h, dt, nt, order) -> Grid:
-    return Grid(int(ndim), int(nx), int(ny), int(nz), int(nt), int(order), float(h), float(dt))
+def make_grid(ndim, nx, ny, nz, h, dt, nt, order, sponge=0, sponge_eta=0.0) -> Grid:
+    """sponge / sponge_eta: width (cells) and peak damping [1/s] of the
+    absorbing layer on every face (0: none)."""
+    return Grid(int(ndim), int(nx), int(ny), int(nz), int(nt), int(order), float(h), float(dt),
+                int(sponge), float(sponge_eta))
 
 
 def grid_of(w, nt=None) -> Grid:
     """Grid of a ``workloads.Workload`` (optionally with a truncated nt)."""
-    return make_grid(w.ndim, w.nx, w.ny, w.nz, w.h, w.dt, w.nt if nt is None else nt, w.order)
+    return make_grid(w.ndim, w.nx, w.ny, w.nz, w.h, w.dt, w.nt if nt is None else nt, w.order,
+                     getattr(w, "sponge", 0), getattr(w, "sponge_eta", 0.0))
 
 
 def fd_weights(order: int) -> np.ndarray:

@@ -32,6 +32,16 @@
  *           udd[k] = (u[k] - 2u[k-1] + u[k-2]) / dt^2             (Eq. 3)
  *           with lambda driven by the residual s = R u - d_obs.  Eq. 3 is
  *           printed without a sign; the exact derivative carries a minus.
+ *   sponge: optional absorbing layer (not in the paper): damping m*eta*du/dt
+ *           with eta(x) = eta_max ((w - d)/w)^2 at nodes whose distance d (in
+ *           cells) to the nearest face is below w; every face but the top
+ *           (z = 0), which stays the zero-pressure free surface where sources
+ *           and receivers sit.  The step becomes
+ *             (1+a) u[t+1] = 2u[t] - (1-a) u[t-1] + dt^2 v^2 (L u[t] + S^T q[t]),
+ *           a = eta dt / 2; the time-stepping blocks stay symmetric, so the
+ *           adjoint keeps the same form, and udd above becomes
+ *           udd[k] + eta (u[k] - u[k-2]) / (2 dt) (the derivative of the
+ *           damped system with respect to m).  w = 0 is the undamped scheme.
  *   probed: ubar[x,i] = sum_k Q[k,i] udd[k,x], vbar[x,i] = sum_k Q[k,i]
  *           lambda[k,x], output -scale * sum_i ubar[x,i] vbar[x,i]
  *           (Algorithm 1 lines 2, 6, 8; Eq. 4), scale = 1/r for random
@@ -45,6 +55,8 @@
 typedef struct {
   int ndim, nx, ny, nz, nt, order;
   double h, dt;
+  int sponge;        /* width w of the absorbing layer in cells (0: none) */
+  double sponge_eta; /* eta_max [1/s] */
 } oracle_grid;
 
 #define MAXR 8
@@ -116,11 +128,28 @@ void oracle_laplacian(const oracle_grid* g, const double* u, double* out) {
 
 static long npts(const oracle_grid* g) { return (long)g->nx * g->ny * g->nz; }
 
+/* eta at flat node index p (see the header); 0 without a sponge */
+static double sponge_eta(const oracle_grid* g, long p) {
+  if (g->sponge <= 0) return 0.0;
+  const long x = p % g->nx, y = (p / g->nx) % g->ny, z = p / ((long)g->nx * g->ny);
+  long d = x < g->nx - 1 - x ? x : g->nx - 1 - x;
+  const long dz = g->nz - 1 - z; /* the top face z = 0 stays the free surface */
+  if (dz < d) d = dz;
+  if (g->ndim == 3) {
+    const long dy = y < g->ny - 1 - y ? y : g->ny - 1 - y;
+    if (dy < d) d = dy;
+  }
+  if (d >= g->sponge) return 0.0;
+  const double t = (double)(g->sponge - d) / (double)g->sponge;
+  return g->sponge_eta * t * t;
+}
+
 static double* zalloc(long n) { return (double*)calloc((size_t)n, sizeof(double)); }
 
 /* One time step of operator f (forward) or f^T (adjoint); both have the form
- *   out = 2 cur - old + dt^2 v^2 (L cur + rhs),
- * where rhs is a sparse set of point values added at idx[k]. */
+ *   (1+a) out = 2 cur - (1-a) old + dt^2 v^2 (L cur + rhs),
+ * where rhs is a sparse set of point values added at idx[k] and a = eta dt/2
+ * (zero outside the sponge). */
 static void leapfrog(const oracle_grid* g, const double* vel, const double* cur, const double* old,
                      double* out, double* lap, int nrhs, const int64_t* idx, const double* val) {
   const long N = npts(g);
@@ -128,7 +157,10 @@ static void leapfrog(const oracle_grid* g, const double* vel, const double* cur,
   oracle_laplacian(g, cur, lap);
   for (int k = 0; k < nrhs; ++k) lap[idx[k]] += val[k];
 #pragma omp parallel for schedule(static)
-  for (long x = 0; x < N; ++x) out[x] = 2.0 * cur[x] - old[x] + dt2 * vel[x] * vel[x] * lap[x];
+  for (long x = 0; x < N; ++x) {
+    const double a = 0.5 * sponge_eta(g, x) * g->dt;
+    out[x] = (2.0 * cur[x] - (1.0 - a) * old[x] + dt2 * vel[x] * vel[x] * lap[x]) / (1.0 + a);
+  }
 }
 
 /* ------------------------------------------------------------ operator F */
@@ -205,7 +237,8 @@ int oracle_gradient_full(const oracle_grid* g, int nsrc, const int64_t* src, int
     leapfrog(g, vel, l1, l2, l0, lap, nrec, rec, res + (long)j * nrec);
     const double *a = hist + (long)j * N, *b = hist + (long)(j - 1) * N, *c = hist + (long)(j - 2) * N;
 #pragma omp parallel for schedule(static)
-    for (long x = 0; x < N; ++x) grad[x] -= l0[x] * (a[x] - 2.0 * b[x] + c[x]) * idt2;
+    for (long x = 0; x < N; ++x)
+      grad[x] -= l0[x] * ((a[x] - 2.0 * b[x] + c[x]) * idt2 + sponge_eta(g, x) * (a[x] - c[x]) / (2.0 * g->dt));
     double* tmp = l2; l2 = l1; l1 = l0; l0 = tmp;
   }
   free(hist); free(d); free(res); free(l2); free(l1); free(l0); free(lap);
@@ -233,17 +266,25 @@ int oracle_gradient_probed(const oracle_grid* g, int nsrc, const int64_t* src, i
   double* res = zalloc((long)nt * nrec);
   double *um = zalloc(N), *u0 = zalloc(N), *up = zalloc(N), *lap = zalloc(N);
   double* Qt = zalloc((long)(nt + 2) * r);
-  if (!ubar || !vbar || !d || !res || !um || !u0 || !up || !lap || !Qt) return 1;
+  double* Qd = zalloc((long)(nt + 2) * r);
+  if (!ubar || !vbar || !d || !res || !um || !u0 || !up || !lap || !Qt || !Qd) return 1;
   if (form == 1) {
+    /* u[j] enters udd[k] for k = j, j+1, j+2 with weights 1, -2, 1 (/dt^2)
+     * and the sponge's first difference for k = j, j+2 with +1, -1 (/2dt) */
     for (int j = 0; j < nt; ++j)
       for (int i = 0; i < r; ++i) {
-        double s = 0.0;
+        double s = 0.0, sd = 0.0;
         for (int o = 0; o <= 2; ++o) {
           int k = j + o;
           double wk = (o == 1) ? -2.0 : 1.0;
-          if (k >= 2 && k <= nt - 1) s += wk * Q[(long)k * r + i];
+          double wd = o == 0 ? 1.0 : (o == 2 ? -1.0 : 0.0);
+          if (k >= 2 && k <= nt - 1) {
+            s += wk * Q[(long)k * r + i];
+            sd += wd * Q[(long)k * r + i];
+          }
         }
         Qt[(long)j * r + i] = s * idt2;
+        Qd[(long)j * r + i] = sd / (2.0 * g->dt);
       }
   }
   /* forward propagation, lines 0-3 */
@@ -255,14 +296,17 @@ int oracle_gradient_probed(const oracle_grid* g, int nsrc, const int64_t* src, i
       const double* Qk = Q + (long)k * r;
 #pragma omp parallel for schedule(static)
       for (long x = 0; x < N; ++x) {
-        double udd = (up[x] - 2.0 * u0[x] + um[x]) * idt2;
+        double udd = (up[x] - 2.0 * u0[x] + um[x]) * idt2 + sponge_eta(g, x) * (up[x] - um[x]) / (2.0 * g->dt);
         for (int i = 0; i < r; ++i) ubar[x * r + i] += Qk[i] * udd;
       }
     } else {
       const double* Qk = Qt + (long)k * r;
+      const double* Qdk = Qd + (long)k * r;
 #pragma omp parallel for schedule(static)
-      for (long x = 0; x < N; ++x)
-        for (int i = 0; i < r; ++i) ubar[x * r + i] += Qk[i] * up[x];
+      for (long x = 0; x < N; ++x) {
+        const double eta = sponge_eta(g, x);
+        for (int i = 0; i < r; ++i) ubar[x * r + i] += (Qk[i] + eta * Qdk[i]) * up[x];
+      }
     }
     double* tmp = um; um = u0; u0 = up; up = tmp;
   }
@@ -288,7 +332,7 @@ int oracle_gradient_probed(const oracle_grid* g, int nsrc, const int64_t* src, i
   }
   if (ubar_out) memcpy(ubar_out, ubar, sizeof(double) * N * r);
   if (vbar_out) memcpy(vbar_out, vbar, sizeof(double) * N * r);
-  free(ubar); free(vbar); free(d); free(res); free(um); free(u0); free(up); free(lap); free(Qt);
+  free(ubar); free(vbar); free(d); free(res); free(um); free(u0); free(up); free(lap); free(Qt); free(Qd);
   return 0;
 }
 

@@ -59,6 +59,8 @@ class Workload:
     probe_kind: str = "rademacher"
     seed: int = DEFAULT_SEED
     T: int = 32
+    sponge: int = 0           # absorbing layer width in cells on every face but the top (0: none)
+    sponge_eta: float = 0.0   # its peak damping [1/s]
 
     @property
     def N(self) -> int:
@@ -284,3 +286,18 @@ def synthetic_data(nshots: int, nt: int, nrec: int, seed: int, amp: float = 1e-3
     from scipy.ndimage import convolve1d
     d = convolve1d(d, k / k.sum(), axis=1, mode="constant")
     return (amp * d).astype(np.float32)
+
+
+def sponge_eta_for(vmax: float, width: int, h: float, reflection: float = 1e-3) -> float:
+    """Peak damping of a quadratic absorbing layer of `width` cells: the
+    usual choice 3 v ln(1/R) / (2 L) for a target reflection R over a layer
+    of thickness L = width * h."""
+    return 3.0 * vmax * np.log(1.0 / reflection) / (2.0 * width * h)
+
+
+def with_sponge(w: Workload, width: int, reflection: float = 1e-3) -> Workload:
+    """The workload with an absorbing layer of `width` cells on every face but
+    the top (the free surface, where sources and receivers sit)."""
+    import dataclasses
+    vmax = float(max(w.vel_true.max(), w.vel0.max()))
+    return dataclasses.replace(w, sponge=int(width), sponge_eta=sponge_eta_for(vmax, width, w.h, reflection))
