@@ -102,6 +102,15 @@ typedef struct {
                   so that the rounding of u is integrated once instead of
                   twice (more accurate over thousands of steps, one more
                   4-byte write per point and step) */
+  int sponge;  /* absorbing layer (not in the paper): width in cells on every
+                  face but the top z = 0, which stays the zero-pressure free
+                  surface; 0: none (the undamped scheme, bit for bit).  The
+                  damping m * eta * du/dt, eta = sponge_eta ((w - d)/w)^2 at
+                  distance d < w cells from a damped face, makes the step
+                  (1+a) u[t+1] = 2u[t] - (1-a) u[t-1] + dt^2 v^2 (L u[t] + S^T q[t]),
+                  a = eta dt / 2; the adjoint keeps the same form, and every
+                  gradient is dJ/dm of the damped system */
+  float sponge_eta; /* peak damping eta_max [1/s], >= 0 */
 } tp_grid;
 
 typedef enum { TP_FORM_LEVELS = 0, TP_FORM_INCREMENT = 1 } tp_form;

@@ -56,7 +56,7 @@ class Problem:
     """A batch of shots on one model grid, with device-resident geometry."""
 
     def __init__(self, ndim, nx, ny, nz, h, dt, nt, order, src, rec, vmax: float = 0.0, device="cuda",
-                 form: str = "levels"):
+                 form: str = "levels", sponge: int = 0, sponge_eta: float = 0.0):
         self.device = torch.device(device)
         self.src = torch.as_tensor(src, dtype=torch.int64, device=self.device).contiguous()
         self.rec = torch.as_tensor(rec, dtype=torch.int64, device=self.device).contiguous()
@@ -68,7 +68,7 @@ class Problem:
         if self.rec.shape[0] != self.nshots:
             raise ValueError("src and rec need the same number of shots")
         self.grid = native.tp_grid(int(ndim), int(nx), int(ny), int(nz), float(h), float(dt), int(nt), int(order),
-                                   float(vmax), native.TIME_FORMS[form])
+                                   float(vmax), native.TIME_FORMS[form], int(sponge), float(sponge_eta))
         self.geom = native.tp_geom(self.nshots, int(self.src.shape[1]), self.src.data_ptr(),
                                    int(self.rec.shape[1]), self.rec.data_ptr())
         self._ws = {}
@@ -77,7 +77,8 @@ class Problem:
     def from_workload(cls, w, nt=None, vmax=None, device="cuda", form="levels"):
         vm = float(max(w.vel_true.max(), w.vel0.max())) if vmax is None else vmax
         return cls(w.ndim, w.nx, w.ny, w.nz, w.h, w.dt, w.nt if nt is None else nt, w.order, w.src, w.rec,
-                   vmax=vm, device=device, form=form)
+                   vmax=vm, device=device, form=form, sponge=getattr(w, "sponge", 0),
+                   sponge_eta=getattr(w, "sponge_eta", 0.0))
 
     # ---------------------------------------------------------------- sizes
     @property

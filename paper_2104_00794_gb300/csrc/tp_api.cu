@@ -159,6 +159,8 @@ tp_status check_grid(const tp_grid* g) {
   if (g->nx > (1 << 24) || g->nz > (1 << 24) || g->ny > (1 << 24)) return fail(TP_ERR_ARG, "grid extent too large");
   if (!(g->vmax >= 0.f)) return fail(TP_ERR_ARG, "vmax must be >= 0");
   if (g->form != TP_FORM_LEVELS && g->form != TP_FORM_INCREMENT) return fail(TP_ERR_ARG, "unknown time form %d", g->form);
+  if (g->sponge < 0 || !(g->sponge_eta >= 0.f) || !std::isfinite(g->sponge_eta))
+    return fail(TP_ERR_ARG, "sponge width must be >= 0 and sponge_eta finite and >= 0");
   return TP_OK;
 }
 
@@ -195,6 +197,8 @@ tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe
   P->op = op;
   P->L = make_layout(g->ndim, g->nx, g->ny, g->nz);
   P->W = stencil_weights(g->order);
+  P->W.sw = g->sponge_eta > 0.f ? g->sponge : 0;
+  P->W.samax = (float)(0.5 * (double)g->sponge_eta * (double)g->dt);
   P->nshots = geo->nshots;
   P->nsrc = geo->nsrc;
   P->nrec = geo->nrec;
@@ -306,9 +310,9 @@ tp_status setup(const Ctx& c, const tp_grid* g, const tp_geom* geo, const float*
   TRY(cudaMemsetAsync(c.at<float>(P.o_c2), 0, (size_t)P.L.field * sizeof(float), c.st));
   const double dt2 = (double)g->dt * (double)g->dt;
   TRY(launch_prep_c2(P.L, vel, dt2 / ((double)g->h * (double)g->h), c.at<float>(P.o_c2), c.st));
-  TRY(launch_prep_points(P.L, geo->src, (long long)P.nshots * P.nsrc, vel, dt2, c.at<long long>(P.o_soff),
+  TRY(launch_prep_points(P.L, P.W, geo->src, (long long)P.nshots * P.nsrc, vel, dt2, c.at<long long>(P.o_soff),
                          c.at<float>(P.o_cs), c.err(), c.st));
-  TRY(launch_prep_points(P.L, geo->rec, (long long)P.nshots * P.nrec, vel, dt2, c.at<long long>(P.o_roff),
+  TRY(launch_prep_points(P.L, P.W, geo->rec, (long long)P.nshots * P.nrec, vel, dt2, c.at<long long>(P.o_roff),
                          c.at<float>(P.o_cr), c.err(), c.st));
   float vmax = g->vmax;
   if (!(vmax > 0.f)) {
@@ -533,7 +537,8 @@ tp_status probed_forward_impl(const Ctx& c, const tp_probe* probe, const float* 
 // (= dt^2 v^2 (L P_i + S^T qbar_i)) replaces P_i in place; the adjoint windows
 // fold sum_i ubar_i (Q_w^T lambda)_i into one accumulator field per shot, and
 // grad = -(scale / dt^2) sum_s of it.  Same estimator as the two-set form.
-tp_status probed_backward_fold(const Ctx& c, const tp_grid* grid, const float* vel, const float* wavelet,
+tp_status probed_backward_fold(const Ctx& c, const tp_grid* grid, const tp_geom* geom, const float* vel,
+                               const float* wavelet,
                                const float* s, int wrt_velocity, float* grad, double* gnorm, const float* Q,
                                float* Pacc) {
   const Plan& P = c.P;
@@ -553,8 +558,8 @@ tp_status probed_backward_fold(const Ctx& c, const tp_grid* grid, const float* v
     TRY(cudaMemcpy2DAsync(Pacc + (long long)i * P.L.field, (size_t)P.acc_elems * sizeof(float), tmp, fb, fb,
                           P.nshots, cudaMemcpyDeviceToDevice, c.st));
   }
-  TRY(launch_source_into_acc(c.at<long long>(P.o_soff), c.at<float>(P.o_cs), c.at<float>(P.o_qbar), P.nsrc,
-                             P.nshots, r, Pacc, P.acc_elems, P.L.field, c.st));
+  TRY(launch_source_into_acc(c.at<long long>(P.o_soff), geom->src, vel, (double)grid->dt * (double)grid->dt,
+                             c.at<float>(P.o_qbar), P.nsrc, P.nshots, r, Pacc, P.acc_elems, P.L.field, c.st));
   TRY(cudaMemsetAsync(c.at<float>(P.o_f), 0, (size_t)P.nf * fb, c.st));  // levels nt, nt+1 start at zero
   TRY(cudaMemsetAsync(tmp, 0, (size_t)P.nshots * fb, c.st));
   const Fam ring{P.o_f, (int)P.nf, S};
@@ -614,7 +619,7 @@ tp_status probed_backward_impl(const Ctx& c, const tp_grid* grid, const tp_geom*
                                const float* Q, const void* Pacc) {
   const Plan& P = c.P;
   if (P.acc == TP_ACC_F32_FOLD)
-    return probed_backward_fold(c, grid, vel, wavelet, s, wrt_velocity, grad, gnorm, Q,
+    return probed_backward_fold(c, grid, geom, vel, wavelet, s, wrt_velocity, grad, gnorm, Q,
                                 static_cast<float*>(const_cast<void*>(Pacc)));
   const size_t fb = (size_t)P.L.field * sizeof(float);
   const int nt = P.nt, r = P.r;

@@ -48,7 +48,26 @@ Layout make_layout(int ndim, int nx, int ny, int nz);
 struct Weights {
   float w[5];
   int R;
+  int sw;       // absorbing layer width in cells (0: none)
+  float samax;  // a = eta dt / 2 at the outermost node of the layer
 };
+
+// a = eta dt / 2 of the absorbing layer at node (z, y, x): samax ((sw - d)/sw)^2
+// within sw cells of the bottom and side faces (the top z = 0 is the free
+// surface), 0 elsewhere or without a layer.
+__host__ __device__ inline float sponge_a(const Layout& L, const Weights& W, long long z, long long y, long long x) {
+  if (W.sw <= 0) return 0.f;
+  long long d = x < L.nx - 1 - x ? x : L.nx - 1 - x;
+  const long long dz = L.nz - 1 - z;
+  if (dz < d) d = dz;
+  if (L.ndim == 3) {
+    const long long dy = y < L.ny - 1 - y ? y : L.ny - 1 - y;
+    if (dy < d) d = dy;
+  }
+  if (d >= W.sw) return 0.f;
+  const float t = (float)(W.sw - d) / (float)W.sw;
+  return W.samax * t * t;
+}
 Weights stencil_weights(int order);
 
 // ---------------------------------------------------------------- stencil
@@ -119,7 +138,7 @@ cudaError_t launch_prep_c2(const Layout& L, const float* vel, double coef, float
 cudaError_t launch_vmax(const float* vel, long long n, unsigned int* out_bits, cudaStream_t s);
 // dense node indices -> padded offsets, and injection coefficient dt^2 v^2 at each point
 // (out-of-range indices get offset -1 and set bit 2 of *err)
-cudaError_t launch_prep_points(const Layout& L, const int64_t* idx, long long n, const float* vel,
+cudaError_t launch_prep_points(const Layout& L, const Weights& W, const int64_t* idx, long long n, const float* vel,
                                double dt2, long long* off, float* cinj, int* err, cudaStream_t s);
 
 // One thread per point of two independent sets, all shots:
@@ -153,9 +172,10 @@ cudaError_t launch_finalize_sum(const double* part, int nblk, double scale, doub
 // grad[x] = -scale_h2 * sum_s gacc[s][off(x)]              (times_v2 = 0)
 cudaError_t launch_finish_grad(const Layout& L, const float* vel, const float* gacc, int nshots,
                                long long gacc_ss, float scale_h2, float* grad, cudaStream_t s, int times_v2 = 1);
-// U[s][i][src_off[s][k]] += cinj[s][k] * qbar[s][k][i]   (serial, fixed order)
-cudaError_t launch_source_into_acc(const long long* src_off, const float* cinj, const float* qbar, int nsrc,
-                                   int nshots, int r, float* U, long long u_ss, long long field, cudaStream_t s);
+// U[s][i][src_off[s][k]] += dt^2 v[src[s][k]]^2 * qbar[s][k][i]   (serial, fixed order)
+cudaError_t launch_source_into_acc(const long long* src_off, const int64_t* src, const float* vel, double dt2,
+                                   const float* qbar, int nsrc, int nshots, int r, float* U, long long u_ss,
+                                   long long field, cudaStream_t s);
 // fp32 copy of accumulator field i of every shot: out[s] = value (+ compensation)
 cudaError_t launch_acc_to_f32(const void* P, int acc, int r, int i, long long field, int nshots, float* out,
                               long long out_ss, cudaStream_t s);

@@ -30,7 +30,7 @@ __global__ void vmax_kernel(const float* __restrict__ vel, long long n, unsigned
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as integers
 }
 
-__global__ void prep_points_kernel(Layout L, const int64_t* __restrict__ idx, long long n,
+__global__ void prep_points_kernel(Layout L, Weights W, const int64_t* __restrict__ idx, long long n,
                                    const float* __restrict__ vel, double dt2, long long* __restrict__ off,
                                    float* __restrict__ cinj, int* err) {
   const long long N = (long long)L.nx * L.ny * L.nz;
@@ -43,7 +43,10 @@ __global__ void prep_points_kernel(Layout L, const int64_t* __restrict__ idx, lo
     } else {
       off[i] = L.off_flat(p);
       const double v = vel[p];
-      cinj[i] = (float)(dt2 * v * v);
+      // inside the absorbing layer the injected value is divided by 1 + a like the step
+      const long long x = p % L.nx, y = (p / L.nx) % L.ny, z = p / ((long long)L.nx * L.ny);
+      const double a = (double)sponge_a(L, W, z, y, x);
+      cinj[i] = (float)(dt2 * v * v / (1.0 + a));
     }
   }
 }
@@ -178,16 +181,19 @@ __global__ void finish_grad_kernel(Layout L, const float* __restrict__ vel, cons
   }
 }
 
-__global__ void source_into_acc_kernel(const long long* __restrict__ soff, const float* __restrict__ cinj,
-                                       const float* __restrict__ qbar, int nsrc, int nshots, int r,
-                                       float* __restrict__ U, long long u_ss, long long field) {
+__global__ void source_into_acc_kernel(const long long* __restrict__ soff, const int64_t* __restrict__ src,
+                                       const float* __restrict__ vel, double dt2, const float* __restrict__ qbar,
+                                       int nsrc, int nshots, int r, float* __restrict__ U, long long u_ss,
+                                       long long field) {
   const int i = threadIdx.x;  // one thread per probe column, shots and sources in a fixed order
   if (i >= r || blockIdx.x != 0) return;
   for (int s = 0; s < nshots; ++s)
     for (int k = 0; k < nsrc; ++k) {
       const long long o = soff[(long long)s * nsrc + k];
       if (o < 0) continue;
-      U[s * u_ss + (long long)i * field + o] += cinj[(long long)s * nsrc + k] * qbar[((long long)s * nsrc + k) * r + i];
+      const double v = vel[src[(long long)s * nsrc + k]];
+      const float coef = (float)(dt2 * v * v);  // dt^2 v^2, undamped: the factor of S^T qbar in ubar
+      U[s * u_ss + (long long)i * field + o] += coef * qbar[((long long)s * nsrc + k) * r + i];
     }
 }
 
@@ -277,10 +283,10 @@ cudaError_t launch_vmax(const float* vel, long long n, unsigned int* out, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_points(const Layout& L, const int64_t* idx, long long n, const float* vel, double dt2,
-                               long long* off, float* cinj, int* err, cudaStream_t s) {
+cudaError_t launch_prep_points(const Layout& L, const Weights& W, const int64_t* idx, long long n, const float* vel,
+                               double dt2, long long* off, float* cinj, int* err, cudaStream_t s) {
   prof_before(5, s);
-  prep_points_kernel<<<grid_for(n, 256), 256, 0, s>>>(L, idx, n, vel, dt2, off, cinj, err);
+  prep_points_kernel<<<grid_for(n, 256), 256, 0, s>>>(L, W, idx, n, vel, dt2, off, cinj, err);
   prof_after(5, s);
   return cudaGetLastError();
 }
@@ -325,10 +331,11 @@ cudaError_t launch_finalize_sum(const double* part, int nblk, double scale, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_source_into_acc(const long long* src_off, const float* cinj, const float* qbar, int nsrc,
+cudaError_t launch_source_into_acc(const long long* src_off, const int64_t* src, const float* vel, double dt2,
+                                   const float* qbar, int nsrc,
                                    int nshots, int r, float* U, long long u_ss, long long field, cudaStream_t s) {
   prof_before(5, s);
-  source_into_acc_kernel<<<1, 64, 0, s>>>(src_off, cinj, qbar, nsrc, nshots, r, U, u_ss, field);
+  source_into_acc_kernel<<<1, 64, 0, s>>>(src_off, src, vel, dt2, qbar, nsrc, nshots, r, U, u_ss, field);
   prof_after(5, s);
   return cudaGetLastError();
 }

@@ -35,12 +35,17 @@ __device__ __forceinline__ float4 ld4(const float* base, long long idx) {
   return __ldg(reinterpret_cast<const float4*>(base + idx));
 }
 
-// returns the new value; in MODE_INC also the new increment through *inc
+// returns the new value; in MODE_INC also the new increment through *inc.
+// a: damping of the absorbing layer at this node (0 outside it, where the
+// undamped expressions run unchanged).
 template <int MODE>
-__device__ __forceinline__ float epilogue(float c, float s, float p1, float p2, float* inc) {
-  if (MODE == MODE_STEP) return fmaf(p2, s, 2.0f * c - p1);
+__device__ __forceinline__ float epilogue(float c, float s, float p1, float p2, float* inc, float a) {
+  if (MODE == MODE_STEP) {
+    if (a == 0.f) return fmaf(p2, s, 2.0f * c - p1);
+    return fmaf(p2, s, 2.0f * c - (1.0f - a) * p1) / (1.0f + a);
+  }
   if (MODE == MODE_INC) {
-    *inc = fmaf(p2, s, p1);
+    *inc = a == 0.f ? fmaf(p2, s, p1) : fmaf(p2, s, (1.0f - a) * p1) / (1.0f + a);
     return c + *inc;
   }
   return fmaf(p1, s, p2);
@@ -65,7 +70,7 @@ __device__ __forceinline__ void store_masked(float* out, long long idx, float4 v
 constexpr int T3X = 16;  // float4 columns per tile (64 points)
 constexpr int T3Y = 16;  // rows per tile
 
-template <int R, int MODE>
+template <int R, int MODE, bool DAMP>
 __global__ void __launch_bounds__(T3X * T3Y, 2)
 sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
   __shared__ float4 sm[T3Y + 2 * R][T3X + 2];
@@ -144,7 +149,10 @@ sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
     }
     float res[4], inc[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) res[p] = epilogue<MODE>(v[4 + p], s[p], comp(c1, p), comp(c2, p), &inc[p]);
+    for (int p = 0; p < 4; ++p) {
+      const float ad = (DAMP && MODE != MODE_IMAGE) ? sponge_a(L, W, z, y, x + p) : 0.f;
+      res[p] = epilogue<MODE>(v[4 + p], s[p], comp(c1, p), comp(c2, p), &inc[p], ad);
+    }
     if (y < L.ny && x < L.nx) {
       store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
       if (MODE == MODE_INC)
@@ -159,7 +167,7 @@ sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
 // ------------------------------------------------------------------ 2-D
 constexpr int W2 = 4;  // warps per CTA, each an independent (x strip, z chunk)
 
-template <int R, int MODE>
+template <int R, int MODE, bool DAMP>
 __global__ void __launch_bounds__(32 * W2)
 sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) {
   __shared__ float4 sm[W2][32 + 2];
@@ -220,7 +228,8 @@ sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) 
         const float t = ((v[4 + p + k] - c) + (v[4 + p - k] - c)) + ((comp(q[R + k], p) - c) + (comp(q[R - k], p) - c));
         s = fmaf(W.w[k], t, s);
       }
-      res[p] = epilogue<MODE>(c, s, comp(c1, p), comp(c2, p), &inc[p]);
+      const float ad = (DAMP && MODE != MODE_IMAGE) ? sponge_a(L, W, z, 0, x + p) : 0.f;
+      res[p] = epilogue<MODE>(c, s, comp(c1, p), comp(c2, p), &inc[p], ad);
     }
     if (x < L.nx) {
       store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
@@ -249,7 +258,7 @@ template <int R, int MODE>
 cudaError_t launch3d(const Layout& L, const Weights& W, const PlainArgs& a, cudaStream_t s) {
   static int occ = 0;
   if (occ == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep3d<R, MODE>, T3X * T3Y, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep3d<R, MODE, false>, T3X * T3Y, 0);
     if (occ <= 0) occ = 1;
   }
   const int gx = (L.nx + 4 * T3X - 1) / (4 * T3X), gy = (L.ny + T3Y - 1) / T3Y;
@@ -260,7 +269,8 @@ cudaError_t launch3d(const Layout& L, const Weights& W, const PlainArgs& a, cuda
   const int bz = (L.nz + nzc - 1) / nzc;
   nzc = (L.nz + bz - 1) / bz;
   dim3 grid(gx, gy, nzc * a.nshots), block(T3X, T3Y);
-  sweep3d<R, MODE><<<grid, block, 0, s>>>(L, W, a, bz, nzc);
+  if (MODE != MODE_IMAGE && W.sw > 0) sweep3d<R, MODE, true><<<grid, block, 0, s>>>(L, W, a, bz, nzc);
+  else sweep3d<R, MODE, false><<<grid, block, 0, s>>>(L, W, a, bz, nzc);
   return cudaGetLastError();
 }
 
@@ -275,7 +285,8 @@ cudaError_t launch2d(const Layout& L, const Weights& W, const PlainArgs& a, cuda
   nzc = (L.nz + bz - 1) / bz;
   const int nwarps = nxt * nzc * a.nshots;
   dim3 grid((nwarps + W2 - 1) / W2), block(32, W2);
-  sweep2d<R, MODE><<<grid, block, 0, s>>>(L, W, a, bz, nzc, nxt, nwarps);
+  if (MODE != MODE_IMAGE && W.sw > 0) sweep2d<R, MODE, true><<<grid, block, 0, s>>>(L, W, a, bz, nzc, nxt, nwarps);
+  else sweep2d<R, MODE, false><<<grid, block, 0, s>>>(L, W, a, bz, nzc, nxt, nwarps);
   return cudaGetLastError();
 }
 

@@ -135,7 +135,9 @@ __device__ __forceinline__ Seg segment(const TmaArgs& a, long long item) {
   return s;
 }
 
-template <int R, int MODE, class C>
+// DAMP: the grid has an absorbing layer (the undamped instantiation carries
+// no trace of it)
+template <int R, int MODE, class C, bool DAMP>
 __global__ void __launch_bounds__(NTHREADS, 2)
 sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mP1,
             const __grid_constant__ CUtensorMap mP2, TmaArgs a) {
@@ -289,10 +291,14 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const float c = v[4 + p];
+        // damping of the absorbing layer (0 outside it: the undamped expressions)
+        const float ad = (DAMP && MODE != MODE_IMAGE) ? sponge_a(a.L, a.W, sg.z0 + j, y, x + p) : 0.f;
         if (MODE == MODE_STEP) {
-          res[p] = fmaf(comp(c2, p), s4[p], 2.0f * c - comp(c1, p));
+          res[p] = ad == 0.f ? fmaf(comp(c2, p), s4[p], 2.0f * c - comp(c1, p))
+                             : fmaf(comp(c2, p), s4[p], 2.0f * c - (1.0f - ad) * comp(c1, p)) / (1.0f + ad);
         } else if (MODE == MODE_INC) {
-          inc[p] = fmaf(comp(c2, p), s4[p], comp(c1, p));
+          inc[p] = ad == 0.f ? fmaf(comp(c2, p), s4[p], comp(c1, p))
+                             : fmaf(comp(c2, p), s4[p], (1.0f - ad) * comp(c1, p)) / (1.0f + ad);
           res[p] = c + inc[p];
         } else {
           res[p] = fmaf(comp(c1, p), s4[p], comp(c2, p));
@@ -401,14 +407,21 @@ bool encode_field_map(const Layout& L, const void* base, long long nfields, int 
 
 namespace {
 
+template <int R, int MODE, class C, bool DAMP>
+cudaError_t launch_k(const CUtensorMap& mU, const CUtensorMap& m1, const CUtensorMap& m2, const TmaArgs& t,
+                     long long blocks, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(sweep3d_tma<R, MODE, C, DAMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    attr = true;
+  }
+  sweep3d_tma<R, MODE, C, DAMP><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, t);
+  return cudaGetLastError();
+}
+
 template <int R, int MODE, class C>
 cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
   constexpr int BX = C::BX, BY = C::BY;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(sweep3d_tma<R, MODE, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    attr = true;
-  }
   CUtensorMap mU, m1, m2;
   if (!get_map(L, a.src, C::UW, C::UH, &mU) || !get_map(L, a.p1, BX, BY, &m1) || !get_map(L, a.p2, BX, BY, &m2))
     return cudaErrorInvalidValue;
@@ -448,8 +461,8 @@ cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cu
   t.nzc = (L.nz + t.zchunk - 1) / t.zchunk;
   t.items = cols * t.nzc;
   const long long blocks = std::min<long long>(t.items, slots);
-  sweep3d_tma<R, MODE, C><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, t);
-  return cudaGetLastError();
+  if (MODE != MODE_IMAGE && W.sw > 0) return launch_k<R, MODE, C, true>(mU, m1, m2, t, blocks, s);
+  return launch_k<R, MODE, C, false>(mU, m1, m2, t, blocks, s);
 }
 
 // 64 x 16 tiles, 3 planes of lookahead: 128 x 8, 32 x 32 tiles measured the

@@ -29,7 +29,8 @@ KERNEL_KINDS = 6
 class tp_grid(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_float), ("dt", ctypes.c_float), ("nt", ctypes.c_int), ("order", ctypes.c_int),
-                ("vmax", ctypes.c_float), ("form", ctypes.c_int)]
+                ("vmax", ctypes.c_float), ("form", ctypes.c_int), ("sponge", ctypes.c_int),
+                ("sponge_eta", ctypes.c_float)]
 
 
 class tp_geom(ctypes.Structure):

@@ -93,6 +93,8 @@ def test_folded_accumulators_halve_the_accumulator_memory(L):
     (lambda g, p: setattr(g, "nt", 2), "nt"),
     (lambda g, p: setattr(g, "ny", 3), "ny"),
     (lambda g, p: setattr(g, "h", -1.0), "positive"),
+    (lambda g, p: setattr(g, "sponge", -1), "sponge"),
+    (lambda g, p: setattr(g, "sponge_eta", float("nan")), "sponge"),
     (lambda g, p: setattr(p, "r", 0), "r must"),
     (lambda g, p: setattr(p, "r", 300), "r must"),
     (lambda g, p: setattr(p, "T", 48), "window"),
