@@ -218,18 +218,33 @@ sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) 
     __syncwarp();
     const float4 xl = sm[wi][lane], xc = sm[wi][lane + 1], xr = sm[wi][lane + 2];
     const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
+    // difference form (annihilates constants whatever the weight rounding), two
+    // points per packed fp32x2 instruction: each lane is the scalar operation in
+    // the same order (u[+k] - u as fma(u, -1, u[+k]), exact product), so the
+    // result is bit-identical to the scalar loop
+    float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const float2 neg1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+      const float4 zp = q[R + k], zm = q[R - k];
+      const float2 wk = make_float2(W.w[k], W.w[k]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = 2 * h;
+        const float2 c = make_float2(v[4 + p], v[5 + p]);
+        const float2 dxp = __ffma2_rn(c, neg1, make_float2(v[4 + p + k], v[5 + p + k]));
+        const float2 dxm = __ffma2_rn(c, neg1, make_float2(v[4 + p - k], v[5 + p - k]));
+        const float2 dzp = __ffma2_rn(c, neg1, h ? make_float2(zp.z, zp.w) : make_float2(zp.x, zp.y));
+        const float2 dzm = __ffma2_rn(c, neg1, h ? make_float2(zm.z, zm.w) : make_float2(zm.x, zm.y));
+        s2[h] = __ffma2_rn(wk, __fadd2_rn(__fadd2_rn(dxp, dxm), __fadd2_rn(dzp, dzm)), s2[h]);
+      }
+    }
+    const float s4[4] = {s2[0].x, s2[0].y, s2[1].x, s2[1].y};
     float res[4], inc[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const float c = v[4 + p];
-      float s = 0.f;  // difference form: annihilates constants whatever the weight rounding
-#pragma unroll
-      for (int k = 1; k <= R; ++k) {
-        const float t = ((v[4 + p + k] - c) + (v[4 + p - k] - c)) + ((comp(q[R + k], p) - c) + (comp(q[R - k], p) - c));
-        s = fmaf(W.w[k], t, s);
-      }
       const float ad = (DAMP && MODE != MODE_IMAGE) ? sponge_a(L, W, z, 0, x + p) : 0.f;
-      res[p] = epilogue<MODE>(c, s, comp(c1, p), comp(c2, p), &inc[p], ad);
+      res[p] = epilogue<MODE>(v[4 + p], s4[p], comp(c1, p), comp(c2, p), &inc[p], ad);
     }
     if (x < L.nx) {
       store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
