@@ -71,9 +71,10 @@ def measured_peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-def profile_traffic(kernel_file: str, src_file: str):
+def profile_traffic(kernel_file: str, src_file: str, key: str):
     """dram bytes per launch recorded by an ncu capture in profiles/, if the
-    kernel source has not changed since (hash match); else None."""
+    kernel source has not changed since (hash match) and the capture is of
+    this workload (`applies_to` = key); else None."""
     path = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(path):
         return None
@@ -81,7 +82,8 @@ def profile_traffic(kernel_file: str, src_file: str):
         text = f.read()
     m = re.search(r"dram_bytes_per_launch_full_size\s*=\s*([0-9.eE+]+)", text)
     h = re.search(r"source_sha256\s*=\s*([0-9a-f]+)", text)
-    if not m or not h:
+    a = re.search(r"applies_to\s*=\s*(.+)", text)
+    if not m or not h or not a or a.group(1).strip() != key:
         return None
     with open(os.path.join(ROOT, src_file), "rb") as f:
         cur = hashlib.sha256(f.read()).hexdigest()[:16]
@@ -361,8 +363,11 @@ def main():
     avg_stencil_ms = st["ms"] / max(st["launches"], 1)
     stencil_bytes = STENCIL_BYTES_PER_POINT * w.N * w.nshots
     achieved = stencil_bytes / (avg_stencil_ms * 1e-3) / 1e9
-    traffic = profile_traffic("stencil_step_3d_256cubed.md", "paper_2104_00794_gb300/csrc/tp_sweep3d_tma.cu")
-    gemm_traffic = profile_traffic("probe_gemm_3d_256cubed.md", "paper_2104_00794_gb300/csrc/tp_gemm.cu")
+    key = f"{w.ndim}d {w.nx}^3 r{w.r} T{w.T}" if (w.ndim == 3 and w.nx == w.ny == w.nz) else w.name
+    traffic = profile_traffic("stencil_step_3d_256cubed.md", "paper_2104_00794_gb300/csrc/tp_sweep3d_tma.cu", key)
+    gemm_traffic = profile_traffic("probe_gemm_3d_256cubed.md", "paper_2104_00794_gb300/csrc/tp_gemm.cu", key)
+    if getattr(w, "sponge", 0):  # the captures are of the undamped kernels
+        traffic = None
     gm = kern["probe_gemm_tcgen05"]
     avg_gemm_ms = gm["ms"] / max(gm["launches"], 1)
     # algorithmic bytes of one window GEMM: T snapshots read + r accumulators read and written
