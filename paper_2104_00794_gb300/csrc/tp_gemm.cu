@@ -354,31 +354,44 @@ __device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap* map, i
 // ACC: accumulator storage (0 fp32, 1 bf16, 2 bf16 value + bf16 compensation),
 // or 3: dot mode -- the staged rows are the r forward fields ubar (fp32) and
 // the gradient row, and the tile is folded into the gradient at once.
+// KP: the window's K extent (32 or 64).  Snapshots move and are split in
+// sub-tiles of KS = 32 levels (one stage, one operand buffer each); a window
+// of 64 levels is two sub-tiles whose MMAs accumulate into the same TMEM tile.
+constexpr int KS = 32;
+
 template <int KP, int ACC>
 struct WCfg {
-  static constexpr int NSR = KP == 32 ? 4 : 2;  // snapshot stages
-  static constexpr int NSA = KP == 32 ? 5 : 2;  // accumulator stages
-  static constexpr int NA = KP == 32 ? 2 : 1;   // operand buffers (hi + lo each)
-  static constexpr uint32_t RSTAGE = (uint32_t)KP * TILE_M * 4;
+  static constexpr int NSR = 4;                 // snapshot stages (one sub-tile each)
+  static constexpr int NSA = KP == 32 ? 5 : 4;  // accumulator stages
+  static constexpr int NA = 2;                  // operand buffers (hi + lo each)
+  static constexpr uint32_t RSTAGE = (uint32_t)KS * TILE_M * 4;
   static constexpr uint32_t PROW = (ACC == 0 || ACC == 3) ? TILE_M * 4 : TILE_M * 2;  // one staged row
   static constexpr uint32_t ASTAGE = GRP * PROW * (ACC == 2 ? 2 : 1) + (ACC == 3 ? PROW : 0);
-  static constexpr uint32_t ABYTES = TILE_M * KP * 4;
+  static constexpr uint32_t ABYTES = TILE_M * KS * 4;
   static constexpr uint32_t BBYTES = GRP * KP * 4;
-  // barriers: full_r, empty_r [NSR]; full_a, empty_a [NSA]; aready [NA]; mdone, tfree [2]
-  static constexpr int NBAR = 2 * NSR + 2 * NSA + NA + 4;
+  // barriers: full_r, empty_r [NSR]; full_a, empty_a [NSA]; aready, afree [NA]; mdone, tfree [2]
+  static constexpr int NBAR = 2 * NSR + 2 * NSA + 2 * NA + 4;
   static constexpr size_t SMEM =
       (size_t)NSR * RSTAGE + (size_t)NSA * ASTAGE + (size_t)NA * 2 * ABYTES + 2 * BBYTES + 8 * NBAR + 16;
 };
 
-// mR1 / mR2: the ring (all shots' slots as one field family) with boxes of
-// n1 and nlev - n1 rows, the window's slots before and after the ring wraps;
-// mA: the accumulator family (box: the rows of one shot); mG: the gradient
-// family of the dot mode (box: one row).
+// The window's sub-tiles: rows (levels) of each, the ring slot of its first
+// level and the rows before the ring wraps.
+struct SubTiles {
+  int nsub;
+  int rows[2], slot[2], n1[2];
+};
+
+// mR[j][0] / mR[j][1]: the ring (all shots' slots as one field family) with
+// boxes of sub-tile j's rows before and after the ring wraps; mA: the
+// accumulator family (box: the rows of one shot); mG: the gradient family of
+// the dot mode (box: one row).
 template <int KP, int ACC>
 __global__ void __launch_bounds__(WS_THREADS, 1)
-probe_gemm_ws(const __grid_constant__ CUtensorMap mR1, const __grid_constant__ CUtensorMap mR2,
+probe_gemm_ws(const __grid_constant__ CUtensorMap mR00, const __grid_constant__ CUtensorMap mR01,
+              const __grid_constant__ CUtensorMap mR10, const __grid_constant__ CUtensorMap mR11,
               const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mG, GemmArgs a, int NP,
-              long long ntiles, int n1) {
+              long long ntiles, SubTiles st_) {
   using C = WCfg<KP, ACC>;
   constexpr int NSR = C::NSR, NSA = C::NSA, NA = C::NA;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -390,7 +403,7 @@ probe_gemm_ws(const __grid_constant__ CUtensorMap mR1, const __grid_constant__ C
   uint64_t* bars = reinterpret_cast<uint64_t*>(B_lo + C::BBYTES);
   const uint32_t full_r = smem_u32(bars), empty_r = full_r + 8 * NSR;
   const uint32_t full_a = empty_r + 8 * NSR, empty_a = full_a + 8 * NSA;
-  const uint32_t aready = empty_a + 8 * NSA, mdone = aready + 8 * NA, tfree = mdone + 16;
+  const uint32_t aready = empty_a + 8 * NSA, afree = aready + 8 * NA, mdone = afree + 8 * NA, tfree = mdone + 16;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + C::NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -416,7 +429,10 @@ probe_gemm_ws(const __grid_constant__ CUtensorMap mR1, const __grid_constant__ C
       mbar_init(full_a + 8 * s, 1);
       mbar_init(empty_a + 8 * s, ACC == 3 ? TILE_M : 1);
     }
-    for (int j = 0; j < NA; ++j) mbar_init(aready + 8 * j, TILE_M);
+    for (int j = 0; j < NA; ++j) {
+      mbar_init(aready + 8 * j, TILE_M);
+      mbar_init(afree + 8 * j, 1);
+    }
     for (int j = 0; j < 2; ++j) {
       mbar_init(mdone + 8 * j, 1);
       mbar_init(tfree + 8 * j, ACC == 3 ? TILE_M : 1);
@@ -442,40 +458,50 @@ probe_gemm_ws(const __grid_constant__ CUtensorMap mR1, const __grid_constant__ C
   const uint32_t tmem = *tmem_slot;
 
   const int cy = a.L.ndim == 3 ? H : 0;
+  // sub-tile fields by value (no dynamic indexing, which would go through local memory)
+  const int nsub = st_.nsub;
+  auto sub_rows = [&](int j) { return j == 0 ? st_.rows[0] : st_.rows[1]; };
+  auto sub_slot = [&](int j) { return j == 0 ? st_.slot[0] : st_.slot[1]; };
+  auto sub_n1 = [&](int j) { return j == 0 ? st_.n1[0] : st_.n1[1]; };
   if (warp == 0 || warp == 10) {
     // ------------------------------------------------------------ producers (lane 0 issues):
-    // warp 0 the snapshot rows, warp 10 the accumulator rows (and the gradient row)
+    // warp 0 the snapshot rows (one stage per sub-tile), warp 10 the
+    // accumulator rows (and the gradient row)
     const bool snap = warp == 0;
     const int NS = snap ? NSR : NSA;
     const uint32_t full = snap ? full_r : full_a, empty = snap ? empty_r : empty_a;
-    const int slot0 = a.level0 % a.nslots;
     const int nacc = ACC == 2 ? 2 * a.r : a.r;  // accumulator rows of one shot
-    const uint32_t bytes = snap ? (uint32_t)a.nlev * TILE_M * 4
-                                : (uint32_t)nacc * C::PROW + (ACC == 3 ? C::PROW : 0);
+    const int nper = snap ? nsub : 1;           // stages per tile
     bool ok = true;
-    uint32_t k = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    uint32_t k = 0;  // stages issued
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       const long long row = tile / nxt;
       const int c0 = HX + (int)(tile % nxt) * TILE_M, c1 = (int)(row % a.L.ny) + cy, c2 = (int)(row / a.L.ny) + H;
-      const int st = k % NS;
-      if (k >= (uint32_t)NS) {
-        bool w = true;
-        if (lane == 0) w = mbar_wait_abort(empty + 8 * st, ((k / NS) - 1) & 1, abort_flag);
-        if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) { ok = false; break; }
-      }
-      if (lane == 0) {
-        mbar_expect_tx(full + 8 * st, bytes);
-        if (snap) {
-          const uint32_t dst = smem_u32(rstage0 + st * C::RSTAGE);
-          tma_rows(dst, &mR1, c0, c1, c2, shot * a.nslots + slot0, full + 8 * st);
-          if (n1 < a.nlev) tma_rows(dst + (uint32_t)n1 * TILE_M * 4, &mR2, c0, c1, c2, shot * a.nslots, full + 8 * st);
-        } else {
-          const uint32_t dst = smem_u32(astage0 + st * C::ASTAGE);
-          tma_rows(dst, &mA, c0, c1, c2, shot * nacc, full + 8 * st);
-          if (ACC == 3) tma_rows(dst + (uint32_t)GRP * C::PROW, &mG, c0, c1, c2, shot, full + 8 * st);
+      for (int j = 0; j < nper; ++j, ++k) {
+        const int st = k % NS;
+        if (k >= (uint32_t)NS) {
+          bool w = true;
+          if (lane == 0) w = mbar_wait_abort(empty + 8 * st, ((k / NS) - 1) & 1, abort_flag);
+          if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) { ok = false; break; }
         }
+        if (lane == 0) {
+          if (snap) {
+            mbar_expect_tx(full + 8 * st, (uint32_t)sub_rows(j) * TILE_M * 4);
+            const uint32_t dst = smem_u32(rstage0 + st * C::RSTAGE);
+            const CUtensorMap* m0 = j == 0 ? &mR00 : &mR10;
+            const CUtensorMap* m1 = j == 0 ? &mR01 : &mR11;
+            tma_rows(dst, m0, c0, c1, c2, shot * a.nslots + sub_slot(j), full + 8 * st);
+            if (sub_n1(j) < sub_rows(j))
+              tma_rows(dst + (uint32_t)sub_n1(j) * TILE_M * 4, m1, c0, c1, c2, shot * a.nslots, full + 8 * st);
+          } else {
+            mbar_expect_tx(full + 8 * st, (uint32_t)nacc * C::PROW + (ACC == 3 ? C::PROW : 0));
+            const uint32_t dst = smem_u32(astage0 + st * C::ASTAGE);
+            tma_rows(dst, &mA, c0, c1, c2, shot * nacc, full + 8 * st);
+            if (ACC == 3) tma_rows(dst + (uint32_t)GRP * C::PROW, &mG, c0, c1, c2, shot, full + 8 * st);
+          }
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     if (!ok && lane == 0) atomicOr(a.err, 1);
     // every issued copy must have landed before the CTA exits (bounded waits)
@@ -489,37 +515,45 @@ probe_gemm_ws(const __grid_constant__ CUtensorMap mR1, const __grid_constant__ C
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = idesc_tf32(TILE_M, NP);
-      const uint32_t sbo = KP * 32, lbo = 128;
+      const uint32_t sbo_a = KS * 32, sbo_b = KP * 32, lbo = 128;
       const uint32_t b_hi_u = smem_u32(B_hi), b_lo_u = smem_u32(B_lo);
       bool ok = true;
-      long long issued = -1;
-      uint32_t k = 0;
-      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-        const int ja = k % NA, jt = k & 1;
-        if (!mbar_wait_abort(aready + 8 * ja, (k / NA) & 1, abort_flag)) { ok = false; break; }
+      long long committed = -1;  // last sub-tile whose MMAs were committed to afree
+      uint32_t k = 0, kc = 0;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++k) {
+        const int jt = k & 1;
         if (k >= 2 && !mbar_wait_abort(tfree + 8 * jt, ((k - 2) / 2) & 1, abort_flag)) { ok = false; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a_hi_u = smem_u32(A0 + 2 * ja * C::ABYTES), a_lo_u = a_hi_u + C::ABYTES;
         const uint32_t d = tmem + (uint32_t)(jt * 32);
+        for (int j = 0; j < nsub; ++j, ++kc) {
+          const int ja = kc % NA;
+          if (!mbar_wait_abort(aready + 8 * ja, (kc / NA) & 1, abort_flag)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_hi_u = smem_u32(A0 + 2 * ja * C::ABYTES), a_lo_u = a_hi_u + C::ABYTES;
+          const uint32_t bo = (uint32_t)j * (KS / 4) * 128;  // sub-tile j's K columns in the K = KP layout of B
 #pragma unroll
-        for (int kk = 0; kk < KP / 8; ++kk) {
-          const uint32_t ko = kk * 2 * 128;
-          const uint64_t ah = smem_desc(a_hi_u + ko, lbo, sbo), al = smem_desc(a_lo_u + ko, lbo, sbo);
-          const uint64_t bh = smem_desc(b_hi_u + ko, lbo, sbo), bl = smem_desc(b_lo_u + ko, lbo, sbo);
-          mma_tf32(d, ah, bh, idesc, kk > 0 ? 1u : 0u);
-          mma_tf32(d, al, bh, idesc, 1u);
-          if (a.q_has_lo) mma_tf32(d, ah, bl, idesc, 1u);
+          for (int kk = 0; kk < KS / 8; ++kk) {
+            const uint32_t ko = kk * 2 * 128;
+            const uint64_t ah = smem_desc(a_hi_u + ko, lbo, sbo_a), al = smem_desc(a_lo_u + ko, lbo, sbo_a);
+            const uint64_t bh = smem_desc(b_hi_u + bo + ko, lbo, sbo_b), bl = smem_desc(b_lo_u + bo + ko, lbo, sbo_b);
+            mma_tf32(d, ah, bh, idesc, (j > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(d, al, bh, idesc, 1u);
+            if (a.q_has_lo) mma_tf32(d, ah, bl, idesc, 1u);
+          }
+          // operand buffer ja is free once these MMAs have read it
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(afree + 8 * ja)
+                       : "memory");
+          committed = kc;
         }
+        if (!ok) break;
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mdone + 8 * jt)
                      : "memory");
-        issued = k;
       }
       if (!ok) {
         atomicOr(a.err, 1);
         // let the MMAs already issued finish before TMEM is released (bounded)
-        if (issued >= 0) {
-          const uint32_t kl = (uint32_t)issued;
-          mbar_wait(mdone + 8 * (kl & 1), (kl / 2) & 1);
+        if (committed >= 0) {
+          const uint32_t kl = (uint32_t)committed;
+          mbar_wait(afree + 8 * (kl % NA), (kl / NA) & 1);
         }
       }
     }
@@ -528,32 +562,35 @@ probe_gemm_ws(const __grid_constant__ CUtensorMap mR1, const __grid_constant__ C
     // ------------------------------------------------------------ converters: one point per thread
     const int m = tid - 64;
     bool ok = true;
-    uint32_t k = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-      const int sr = k % NSR, ja = k % NA;
-      if (!mbar_wait_abort(full_r + 8 * sr, (k / NSR) & 1, abort_flag)) { ok = false; break; }
-      if (k >= (uint32_t)NA) {  // the MMAs of tile k - NA have finished reading operand buffer ja
-        const uint32_t kp = k - NA;
-        if (!mbar_wait_abort(mdone + 8 * (kp & 1), (kp / 2) & 1, abort_flag)) { ok = false; break; }
-      }
-      const float* sA = reinterpret_cast<const float*>(rstage0 + sr * C::RSTAGE);
-      unsigned char* A_hi = A0 + 2 * ja * C::ABYTES;
-      unsigned char* A_lo = A_hi + C::ABYTES;
+    uint32_t kc = 0;  // sub-tiles converted
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int j = 0; j < nsub; ++j, ++kc) {
+        const int sr = kc % NSR, ja = kc % NA;
+        if (!mbar_wait_abort(full_r + 8 * sr, (kc / NSR) & 1, abort_flag)) { ok = false; break; }
+        if (kc >= (uint32_t)NA) {  // the MMAs of sub-tile kc - NA have finished reading operand buffer ja
+          const uint32_t kp = kc - NA;
+          if (!mbar_wait_abort(afree + 8 * ja, (kp / NA) & 1, abort_flag)) { ok = false; break; }
+        }
+        const float* sA = reinterpret_cast<const float*>(rstage0 + sr * C::RSTAGE);
+        unsigned char* A_hi = A0 + 2 * ja * C::ABYTES;
+        unsigned char* A_lo = A_hi + C::ABYTES;
+        const int rows = sub_rows(j);
 #pragma unroll
-      for (int k4 = 0; k4 < KP; k4 += 4) {
-        float v[4];
+        for (int k4 = 0; k4 < KS; k4 += 4) {
+          float v[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = (k4 + j < a.nlev) ? sA[(k4 + j) * TILE_M + m] : 0.f;
-        float4 hi, lo;
-        hi.x = tf32_hi(v[0]); hi.y = tf32_hi(v[1]); hi.z = tf32_hi(v[2]); hi.w = tf32_hi(v[3]);
-        lo.x = v[0] - hi.x; lo.y = v[1] - hi.y; lo.z = v[2] - hi.z; lo.w = v[3] - hi.w;
-        const uint32_t o = kmaj_off(m, k4, KP);
-        *reinterpret_cast<float4*>(A_hi + o) = hi;
-        *reinterpret_cast<float4*>(A_lo + o) = lo;
+          for (int q = 0; q < 4; ++q) v[q] = (k4 + q < rows) ? sA[(k4 + q) * TILE_M + m] : 0.f;
+          float4 hi, lo;
+          hi.x = tf32_hi(v[0]); hi.y = tf32_hi(v[1]); hi.z = tf32_hi(v[2]); hi.w = tf32_hi(v[3]);
+          lo.x = v[0] - hi.x; lo.y = v[1] - hi.y; lo.z = v[2] - hi.z; lo.w = v[3] - hi.w;
+          const uint32_t o = kmaj_off(m, k4, KS);
+          *reinterpret_cast<float4*>(A_hi + o) = hi;
+          *reinterpret_cast<float4*>(A_lo + o) = lo;
+        }
+        mbar_arrive(empty_r + 8 * sr);  // this thread's reads of the snapshot stage are done
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(aready + 8 * ja);
       }
-      mbar_arrive(empty_r + 8 * sr);  // this thread's reads of the snapshot stage are done
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(aready + 8 * ja);
     }
     if (!ok && m == 0) atomicOr(a.err, 1);
   } else {
@@ -669,18 +706,27 @@ cudaError_t launch_ws(const GemmArgs& a, cudaStream_t s) {
   const long long ntiles = (long long)a.L.nz * a.L.ny * ((a.L.nx + TILE_M - 1) / TILE_M);
   const long long grid_x = std::min<long long>(ntiles, (long long)sms);  // one CTA per SM
   dim3 grid((unsigned)grid_x, a.nshots);
-  // the window's slots, split where the ring wraps
-  const int slot0 = a.level0 % a.nslots;
-  const int n1 = std::min(a.nlev, a.nslots - slot0), n2 = a.nlev - n1;
+  // the window's sub-tiles of KS levels, each split where the ring wraps
+  SubTiles sub{};
+  sub.nsub = (a.nlev + KS - 1) / KS;
   const int esize = (ACC == 1 || ACC == 2) ? 2 : 4;
   const int nacc = ACC == 2 ? 2 * a.r : a.r;
-  CUtensorMap mR1, mR2, mA, mG;
-  if (!encode_field_map(a.L, a.ring, (long long)a.nshots * a.nslots, 4, TILE_M, 1, n1, &mR1) ||
-      !encode_field_map(a.L, a.ring, (long long)a.nshots * a.nslots, 4, TILE_M, 1, n2 > 0 ? n2 : 1, &mR2) ||
-      !encode_field_map(a.L, a.P, (long long)a.nshots * nacc, esize, TILE_M, 1, nacc, &mA) ||
+  CUtensorMap mR[2][2], mA, mG;
+  for (int j = 0; j < 2; ++j) {
+    const int jj = j < sub.nsub ? j : 0;  // unused second sub-tile: copies of the first's maps
+    sub.rows[j] = std::min(KS, a.nlev - KS * jj);
+    sub.slot[j] = (a.level0 + KS * jj) % a.nslots;
+    sub.n1[j] = std::min(sub.rows[j], a.nslots - sub.slot[j]);
+    const int n2 = sub.rows[j] - sub.n1[j];
+    if (!encode_field_map(a.L, a.ring, (long long)a.nshots * a.nslots, 4, TILE_M, 1, sub.n1[j], &mR[j][0]) ||
+        !encode_field_map(a.L, a.ring, (long long)a.nshots * a.nslots, 4, TILE_M, 1, n2 > 0 ? n2 : 1, &mR[j][1]))
+      return cudaErrorInvalidValue;
+  }
+  if (!encode_field_map(a.L, a.P, (long long)a.nshots * nacc, esize, TILE_M, 1, nacc, &mA) ||
       !encode_field_map(a.L, ACC == 3 ? (const void*)a.G : a.P, a.nshots, 4, TILE_M, 1, 1, &mG))
     return cudaErrorInvalidValue;
-  probe_gemm_ws<KP, ACC><<<grid, WS_THREADS, C::SMEM, s>>>(mR1, mR2, mA, mG, a, NP, ntiles, n1);
+  probe_gemm_ws<KP, ACC><<<grid, WS_THREADS, C::SMEM, s>>>(mR[0][0], mR[0][1], mR[1][0], mR[1][1], mA, mG, a, NP,
+                                                             ntiles, sub);
   return cudaGetLastError();
 }
 
