@@ -231,6 +231,63 @@ class Problem:
         native.tp_workspace_status(p, buf.numel() - 256, _stream())
 
 
+class GraphedGradient:
+    """One Problem's gradient captured once as a CUDA graph and replayed per call.
+
+    Every kernel of the gradient is enqueued by the library without host
+    synchronisation (given the grid's vmax), so the whole call -- a few
+    thousand kernels for nt = 2000 -- is captured once and launched as one
+    graph.  Inputs (host tensors, preferably pinned, or device tensors) are
+    copied into the graph's static device buffers, the graph is replayed on
+    the current stream, and the gradient and (misfit, |g|) are copied into
+    the caller's outputs when given (else the static device tensors are
+    returned, overwritten by the next call).  The probes are fixed at capture
+    (the spec's seed); use a new GraphedGradient for new probes."""
+
+    def __init__(self, problem: Problem, probe: Optional[ProbeSpec] = None, full: bool = False):
+        if not problem.grid.vmax > 0.0:
+            raise ValueError("a graphed gradient needs the grid's vmax (no host synchronisation inside the call)")
+        if not full and probe is None:
+            raise ValueError("probe spec required for the probed gradient")
+        self.problem, self.probe, self.full = problem, probe, full
+        g, dev = problem.grid, problem.device
+        shape = problem.shape
+        self.vel = torch.ones(shape, dtype=torch.float32, device=dev)
+        self.vel.mul_(float(g.vmax))
+        self.wavelet = torch.zeros((problem.nshots, problem.nt, problem.geom.nsrc), dtype=torch.float32, device=dev)
+        self.d_obs = torch.zeros((problem.nshots, problem.nt, problem.geom.nrec), dtype=torch.float32, device=dev)
+        self.grad = torch.empty(shape, dtype=torch.float32, device=dev)
+        self.scalars = torch.empty(2, dtype=torch.float64, device=dev)
+        self._run()  # allocates the workspace outside the capture
+        torch.cuda.synchronize(dev)
+        side = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(side):
+            self.graph = torch.cuda.CUDAGraph()
+            self.graph.capture_begin()
+            self._run()
+            self.graph.capture_end()
+        torch.cuda.synchronize(dev)
+
+    def _run(self):
+        if self.full:
+            self.problem.gradient_full(self.vel, self.wavelet, self.d_obs, grad=self.grad, scalars=self.scalars)
+        else:
+            self.problem.gradient_probed(self.vel, self.wavelet, self.d_obs, self.probe, grad=self.grad,
+                                         scalars=self.scalars)
+
+    def __call__(self, vel, wavelet, d_obs, grad_out: Optional[torch.Tensor] = None,
+                 scalars_out: Optional[torch.Tensor] = None):
+        self.vel.copy_(vel, non_blocking=True)
+        self.wavelet.copy_(wavelet, non_blocking=True)
+        self.d_obs.copy_(d_obs, non_blocking=True)
+        self.graph.replay()
+        if grad_out is not None:
+            grad_out.copy_(self.grad, non_blocking=True)
+        if scalars_out is not None:
+            scalars_out.copy_(self.scalars, non_blocking=True)
+        return (self.grad if grad_out is None else grad_out), (self.scalars if scalars_out is None else scalars_out)
+
+
 def memory_model(problem: Problem, probe: ProbeSpec) -> dict:
     """Gradient memory: the paper's counts (N nt values for the history,
     2 N r for the probed accumulators) and this library's workspace bytes."""

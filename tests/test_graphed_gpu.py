@@ -1,0 +1,52 @@
+"""The graphed public call (api.GraphedGradient): one capture, replays with new
+inputs.  Every kernel is deterministic (fixed work split, fixed-order
+reductions), so a replay must equal the eager call bit for bit, for host
+(pinned) and device inputs, for consecutive calls with different models, and
+for the probed and the full-storage gradient."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2104_00794_gb300 import api
+from paper_2104_00794_gb300 import workloads as wl
+from parity_util import oracle_dobs, problem, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _lib(cuda_lib):
+    yield
+
+
+@pytest.mark.parametrize("full", [False, True], ids=["probed", "full"])
+@pytest.mark.parametrize("mk", [lambda: wl.small_2d(nx=300, nz=70, nt=220, order=8, nshots=2, r=8),
+                                lambda: wl.small_3d(nx=70, ny=37, nz=45, nt=90, order=8, nshots=2, r=8)],
+                         ids=["2d", "3d"])
+def test_graphed_gradient_equals_eager(mk, full):
+    w = mk()
+    p = problem(w)
+    dobs = oracle_dobs(w)
+    spec = api.ProbeSpec(kind="rademacher", r=8, T=32, seed=w.seed)
+    gg = api.GraphedGradient(p, None if full else spec, full=full)
+    h_out = torch.empty(p.shape, dtype=torch.float32).pin_memory()
+    h_sc = torch.empty(2, dtype=torch.float64).pin_memory()
+    for vel in (w.vel0, w.vel_true):  # two calls in a row with different inputs
+        h_vel = torch.from_numpy(np.ascontiguousarray(vel)).pin_memory()
+        h_wav = torch.from_numpy(np.ascontiguousarray(w.wavelet)).pin_memory()
+        h_d = torch.from_numpy(np.ascontiguousarray(dobs)).pin_memory()
+        gg(h_vel, h_wav, h_d, grad_out=h_out, scalars_out=h_sc)
+        torch.cuda.synchronize()
+        args = (to_dev(vel), to_dev(w.wavelet), to_dev(dobs))
+        ge, se = p.gradient_full(*args) if full else p.gradient_probed(*args, spec)
+        assert torch.equal(h_out, ge.cpu())
+        assert torch.equal(h_sc, se.cpu())
+        gd, sd = gg(*args)  # device inputs, static outputs
+        assert torch.equal(gd, ge) and torch.equal(sd, se)
+
+
+def test_graphed_gradient_needs_vmax():
+    w = wl.small_2d(nx=67, nz=45, nt=60, order=4)
+    p = api.Problem.from_workload(w, vmax=0.0)
+    with pytest.raises(ValueError, match="vmax"):
+        api.GraphedGradient(p, api.ProbeSpec(r=4))
