@@ -246,6 +246,9 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
         if (lane == 0) bar_arrive(emptyU + 8 * s);
       }
     }
+    // unrolled by the queue length (leapfrog and imaging sweeps): the register queue is
+    // renamed instead of shifted (32 moves per plane; 63.6 -> 59.5 us per 256^3 step)
+#pragma unroll((MODE != MODE_INC && !DAMP) ? 2 * R + 1 : 1)
     for (int j = 0; j < nzs && ok; ++j) {
       const uint32_t kc = ku + j + R, kn = ku + j + 2 * R, kq = kp + j;
       const uint32_t sc = kc % C::NSU, sn = kn % C::NSU, sp = kq % C::NSP;
