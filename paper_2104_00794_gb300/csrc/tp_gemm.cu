@@ -4,20 +4,24 @@
 // (lines 2 and 6).  Over a window of T levels this is the dense contraction
 //     P[x, i] += sum_{k in window} W[x, k] * Q[k, i],
 // M = grid points (10^4 .. 2*10^7), K = T (32/64), N = r (4..256), with W the
-// T ring snapshots that the stencil sweeps already wrote.  Per CTA tile of 128
-// points:
-//   1. 128 threads load the tile's T snapshot values (coalesced rows of 128
-//      points per level), split each fp32 value into tf32 hi + lo parts and
-//      store both into shared memory in the K-major, no-swizzle core-matrix
-//      layout (8 rows x 16 B core matrices);
-//   2. one thread issues tcgen05.mma kind::tf32 (M=128, N=round16(r), K=8 per
-//      instruction): hi*Qhi + lo*Qhi (+ hi*Qlo for probes that are not exact
-//      in tf32), accumulating in TMEM;
-//   3. tcgen05.commit arrives on an mbarrier; all warps wait (bounded), read
-//      their 32 TMEM lanes with tcgen05.ld and add the tile into P in HBM.
+// T ring snapshots that the stencil sweeps already wrote.  Every tile of 128
+// points splits its fp32 snapshots into tf32 hi + lo parts in shared memory
+// (K-major, no-swizzle core-matrix layout: 8 rows x 16 B core matrices), one
+// thread issues tcgen05.mma kind::tf32 (M=128, N=round16(r), K=8 per
+// instruction: hi*Qhi + lo*Qhi, + hi*Qlo for probes that are not exact in
+// tf32) into TMEM, and the tile is read back with tcgen05.ld and added to P.
 // The hi/lo split keeps ~22 significant bits of the snapshots, so the product
 // is accurate to a few 1e-7 relative; Rademacher / identity probes are exact
 // in tf32 and skip the third MMA.
+//
+// Two kernels:
+//   * probe_gemm_ws (r <= 32, every accumulator storage and the dot mode of
+//     the single-accumulator adjoint): a warp-specialised pipeline with 4-D
+//     TMA tensor copies and stores, one CTA per SM; described where it is
+//     defined below.  It runs at the HBM roofline.
+//   * probe_gemm_tf32 (r > 32, e.g. identity probes with r = nt in tests):
+//     128 threads per tile load the snapshots through registers, one thread
+//     issues the MMAs, all threads drain TMEM into P.
 #include <cuda_bf16.h>
 
 #include <algorithm>
