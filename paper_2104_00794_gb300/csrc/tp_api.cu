@@ -530,17 +530,13 @@ tp_status probed_forward_impl(const Ctx& c, const tp_probe* probe, const float* 
   return forward_loop(c, ring, level, wavelet, d, fwd_after);
 }
 
-// Algorithm 1 lines 4-8: adjoint sweep driven by s (all shots), vbar_i =
-// sum_{k=2}^{nt-1} Q[k, i] lambda[k], then grad = -scale sum_i ubar_i vbar_i
-// (dJ/dm, or dJ/dv when wrt_velocity) and its fp64 norm.
 // Single-accumulator form (TP_ACC_F32_FOLD): ubar_i = c2 S(P_i) + dt^2 v^2 S^T qbar_i
 // (= dt^2 v^2 (L P_i + S^T qbar_i)) replaces P_i in place; the adjoint windows
 // fold sum_i ubar_i (Q_w^T lambda)_i into one accumulator field per shot, and
 // grad = -(scale / dt^2) sum_s of it.  Same estimator as the two-set form.
 tp_status probed_backward_fold(const Ctx& c, const tp_grid* grid, const tp_geom* geom, const float* vel,
-                               const float* wavelet,
-                               const float* s, int wrt_velocity, float* grad, double* gnorm, const float* Q,
-                               float* Pacc) {
+                               const float* wavelet, const float* s, int wrt_velocity, float* grad, double* gnorm,
+                               const float* Q, float* Pacc) {
   const Plan& P = c.P;
   const size_t fb = (size_t)P.L.field * sizeof(float);
   const int nt = P.nt, T = P.T, S = P.S, r = P.r;
@@ -614,6 +610,9 @@ tp_status adjoint_probes(const Ctx& c, const float* s, const float* Q) {
   return adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after);
 }
 
+// Algorithm 1 lines 4-8: adjoint sweep driven by s (all shots), vbar_i =
+// sum_{k=2}^{nt-1} Q[k, i] lambda[k], then grad = -scale sum_i ubar_i vbar_i
+// (dJ/dm, or dJ/dv when wrt_velocity) and its fp64 norm.
 tp_status probed_backward_impl(const Ctx& c, const tp_grid* grid, const tp_geom* geom, const float* vel,
                                const float* wavelet, const float* s, int wrt_velocity, float* grad, double* gnorm,
                                const float* Q, const void* Pacc) {
