@@ -35,17 +35,17 @@ def _run(w, spec, cond, adj):
     return img, p
 
 
-@pytest.mark.parametrize("w_kw,kind,r", [
-    (dict(nx=300, nz=70, nt=220, order=8, nshots=2), "rademacher", 8),
-    (dict(nx=67, nz=45, nt=160, order=4, nshots=1), "gaussian", 16),
-    (dict(nx=70, ny=37, nz=45, nt=90, order=8, nshots=2), "rademacher", 8),
-    (dict(nx=36, ny=22, nz=28, nt=80, order=4, nshots=1), "gaussian", 32),
-], ids=["2d_rad8", "2d_o4_gau16", "3d_rad8", "3d_o4_gau32"])
+@pytest.mark.parametrize("w_kw,kind,r,T", [
+    (dict(nx=300, nz=70, nt=220, order=8, nshots=2), "rademacher", 8, 32),
+    (dict(nx=67, nz=45, nt=160, order=4, nshots=1), "gaussian", 16, 64),
+    (dict(nx=70, ny=37, nz=45, nt=90, order=8, nshots=2), "rademacher", 8, 32),
+    (dict(nx=36, ny=22, nz=28, nt=80, order=4, nshots=1), "gaussian", 32, 64),
+], ids=["2d_rad8", "2d_o4_gau16_T64", "3d_rad8", "3d_o4_gau32_T64"])
 @pytest.mark.parametrize("cond", ["correlation", "gradient"])
-def test_probed_image_matches_oracle(w_kw, kind, r, cond):
+def test_probed_image_matches_oracle(w_kw, kind, r, T, cond):
     w = (wl.small_3d if "ny" in w_kw else wl.small_2d)(**w_kw, r=r, probe_kind=kind)
     adj = wl.synthetic_data(w.nshots, w.nt, w.nrec, seed=23)
-    spec = api.ProbeSpec(kind=kind, r=r, T=32, seed=w.seed)
+    spec = api.ProbeSpec(kind=kind, r=r, T=T, seed=w.seed)
     img, p = _run(w, spec, cond, adj)
     ref = oracle.batch_image(w, w.vel0, adj.astype(np.float64), cond, kind=kind, r=r, seed=w.seed)
     assert np.linalg.norm(ref) > 0

@@ -82,7 +82,7 @@ def test_gradients_with_sponge(mk):
     ref_f, _ = oracle.batch_gradient_full(w, w.vel0, dobs)
     assert rel_l2(host(gf), ref_f) <= GRAD_TOL, rel_l2(host(gf), ref_f)
     ref_p, _ = oracle.batch_gradient_probed(w, w.vel0, dobs, kind="rademacher", r=8, seed=w.seed)
-    for acc in ("f32", "f32_fold"):
-        gp, _ = p.gradient_probed(*args, api.ProbeSpec(kind="rademacher", r=8, T=32, seed=w.seed, acc=acc))
-        assert rel_l2(host(gp), ref_p) <= GRAD_TOL, (acc, rel_l2(host(gp), ref_p))
+    for acc, T in (("f32", 32), ("f32_fold", 32), ("f32", 64), ("f32_fold", 64)):
+        gp, _ = p.gradient_probed(*args, api.ProbeSpec(kind="rademacher", r=8, T=T, seed=w.seed, acc=acc))
+        assert rel_l2(host(gp), ref_p) <= GRAD_TOL, (acc, T, rel_l2(host(gp), ref_p))
     p.status(native.OP_GRADIENT_PROBED)
