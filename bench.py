@@ -233,7 +233,7 @@ def run_serving(args, rank):
     import torch
     from paper_2104_00794_gb300 import api, serve
     mix = serving_mix(args.serve_requests, seed=wl_seed() + 17 * rank)
-    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")  # copies (inputs may be read-only)
     jobs = []
     for w in mix:
         p = api.Problem.from_workload(w)
@@ -292,7 +292,7 @@ def main():
 
     w = make_workload(args, seed_offset=reps.seed_offset())
     p = api.Problem.from_workload(w, form=args.form)
-    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")  # copies (inputs may be read-only)
     vel_true, vel0, wav = dev(w.vel_true), dev(w.vel0), dev(w.wavelet)
     d_obs = p.forward(vel_true, wav).clone()  # observed data of the true model (setup, untimed)
     probe = api.ProbeSpec(kind=w.probe_kind, r=w.r, T=w.T, seed=w.seed, acc=args.acc)
