@@ -259,6 +259,10 @@ class GraphedGradient:
         self.grad = torch.empty(shape, dtype=torch.float32, device=dev)
         self.scalars = torch.empty(2, dtype=torch.float64, device=dev)
         self._run()  # allocates the workspace outside the capture
+        # the graph keeps raw pointers into the workspace: hold it, so that
+        # problem.release() cannot free it under the graph
+        op = native.OP_GRADIENT_FULL if full else native.OP_GRADIENT_PROBED
+        self._ws = problem._ws[op]
         torch.cuda.synchronize(dev)
         side = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(side):

@@ -45,6 +45,23 @@ def test_graphed_gradient_equals_eager(mk, full):
         assert torch.equal(gd, ge) and torch.equal(sd, se)
 
 
+def test_graphed_gradient_survives_problem_release():
+    """The graph holds the workspace: releasing the Problem's cache does not free it."""
+    w = wl.small_2d(nx=300, nz=70, nt=120, order=8, nshots=1, r=8)
+    p = problem(w)
+    dobs = oracle_dobs(w)
+    spec = api.ProbeSpec(kind="rademacher", r=8, T=32, seed=w.seed)
+    gg = api.GraphedGradient(p, spec)
+    args = (to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs))
+    g1, _ = gg(*args)
+    g1 = g1.clone()
+    p.release()
+    junk = torch.full((1 << 24,), 7.0, device="cuda")  # reuse freed memory if any was freed
+    g2, _ = gg(*args)
+    assert torch.equal(g1, g2)
+    del junk
+
+
 def test_graphed_gradient_needs_vmax():
     w = wl.small_2d(nx=67, nz=45, nt=60, order=4)
     p = api.Problem.from_workload(w, vmax=0.0)
