@@ -129,7 +129,8 @@ typedef struct {
 typedef struct {
   int kind;            /* tp_probe_kind */
   int r;               /* probing vectors, 1..256 (== nt for IDENTITY) */
-  int T;               /* time window of the probe GEMM: 32 or 64 levels */
+  int T;               /* time window of the probe GEMM: 32, 64 or 128 levels
+                          (128 needs r <= 32); the ring holds T + 2 levels */
   uint64_t seed;       /* SplitMix64 seed (random kinds) */
   const float* Z_user; /* device [nshots][nt][r] when kind == TP_PROBE_USER */
   float scale;         /* estimator scale; 0 selects the default: 1/r for

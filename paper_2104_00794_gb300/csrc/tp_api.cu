@@ -182,7 +182,8 @@ tp_status check_probe(const tp_probe* p, int nt) {
   if (p->r < 1 || p->r > 256) return fail(TP_ERR_ARG, "r must be in 1..256 (got %d)", p->r);
   if (p->kind == TP_PROBE_IDENTITY && p->r != nt) return fail(TP_ERR_ARG, "identity probes need r == nt");
   if (p->kind == TP_PROBE_USER && !p->Z_user) return fail(TP_ERR_ARG, "user probes need Z_user");
-  if (p->T != 32 && p->T != 64) return fail(TP_ERR_ARG, "window T must be 32 or 64 (got %d)", p->T);
+  if (p->T != 32 && p->T != 64 && p->T != 128) return fail(TP_ERR_ARG, "window T must be 32, 64 or 128 (got %d)", p->T);
+  if (p->T == 128 && p->r > 32) return fail(TP_ERR_ARG, "window T = 128 needs r <= 32 (got %d)", p->r);
   if (!(p->scale >= 0.f)) return fail(TP_ERR_ARG, "scale must be >= 0");
   return TP_OK;
 }

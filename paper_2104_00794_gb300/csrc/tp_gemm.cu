@@ -358,15 +358,17 @@ __device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap* map, i
 // ACC: accumulator storage (0 fp32, 1 bf16, 2 bf16 value + bf16 compensation),
 // or 3: dot mode -- the staged rows are the r forward fields ubar (fp32) and
 // the gradient row, and the tile is folded into the gradient at once.
-// KP: the window's K extent (32 or 64).  Snapshots move and are split in
-// sub-tiles of KS = 32 levels (one stage, one operand buffer each); a window
-// of 64 levels is two sub-tiles whose MMAs accumulate into the same TMEM tile.
+// KP: the window's K extent (32, 64 or 128).  Snapshots move and are split
+// in sub-tiles of KS = 32 levels (one stage, one operand buffer each); a
+// longer window is several sub-tiles whose MMAs accumulate into the same
+// TMEM tile.
 constexpr int KS = 32;
+constexpr int MAXSUB = 4;
 
 template <int KP, int ACC>
 struct WCfg {
   static constexpr int NSR = 4;                 // snapshot stages (one sub-tile each)
-  static constexpr int NSA = KP == 32 ? 5 : 4;  // accumulator stages
+  static constexpr int NSA = KP == 32 ? 5 : (KP == 64 ? 4 : 3);  // accumulator stages
   static constexpr int NA = 2;                  // operand buffers (hi + lo each)
   static constexpr uint32_t RSTAGE = (uint32_t)KS * TILE_M * 4;
   static constexpr uint32_t PROW = (ACC == 0 || ACC == 3) ? TILE_M * 4 : TILE_M * 2;  // one staged row
@@ -383,10 +385,10 @@ struct WCfg {
 // level and the rows before the ring wraps.
 struct SubTiles {
   int nsub;
-  int rows[2], slot[2], n1[2];
+  int rows[MAXSUB], slot[MAXSUB], n1[MAXSUB];
 };
 
-// mR[j][0] / mR[j][1]: the ring (all shots' slots as one field family) with
+// mRj0 / mRj1: the ring (all shots' slots as one field family) with
 // boxes of sub-tile j's rows before and after the ring wraps; mA: the
 // accumulator family (box: the rows of one shot); mG: the gradient family of
 // the dot mode (box: one row).
@@ -394,6 +396,8 @@ template <int KP, int ACC>
 __global__ void __launch_bounds__(WS_THREADS, 1)
 probe_gemm_ws(const __grid_constant__ CUtensorMap mR00, const __grid_constant__ CUtensorMap mR01,
               const __grid_constant__ CUtensorMap mR10, const __grid_constant__ CUtensorMap mR11,
+              const __grid_constant__ CUtensorMap mR20, const __grid_constant__ CUtensorMap mR21,
+              const __grid_constant__ CUtensorMap mR30, const __grid_constant__ CUtensorMap mR31,
               const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mG, GemmArgs a, int NP,
               long long ntiles, SubTiles st_) {
   using C = WCfg<KP, ACC>;
@@ -464,9 +468,10 @@ probe_gemm_ws(const __grid_constant__ CUtensorMap mR00, const __grid_constant__ 
   const int cy = a.L.ndim == 3 ? H : 0;
   // sub-tile fields by value (no dynamic indexing, which would go through local memory)
   const int nsub = st_.nsub;
-  auto sub_rows = [&](int j) { return j == 0 ? st_.rows[0] : st_.rows[1]; };
-  auto sub_slot = [&](int j) { return j == 0 ? st_.slot[0] : st_.slot[1]; };
-  auto sub_n1 = [&](int j) { return j == 0 ? st_.n1[0] : st_.n1[1]; };
+  auto pick = [](int j, int v0, int v1, int v2, int v3) { return j == 0 ? v0 : (j == 1 ? v1 : (j == 2 ? v2 : v3)); };
+  auto sub_rows = [&](int j) { return pick(j, st_.rows[0], st_.rows[1], st_.rows[2], st_.rows[3]); };
+  auto sub_slot = [&](int j) { return pick(j, st_.slot[0], st_.slot[1], st_.slot[2], st_.slot[3]); };
+  auto sub_n1 = [&](int j) { return pick(j, st_.n1[0], st_.n1[1], st_.n1[2], st_.n1[3]); };
   if (warp == 0 || warp == 10) {
     // ------------------------------------------------------------ producers (lane 0 issues):
     // warp 0 the snapshot rows (one stage per sub-tile), warp 10 the
@@ -492,8 +497,8 @@ probe_gemm_ws(const __grid_constant__ CUtensorMap mR00, const __grid_constant__ 
           if (snap) {
             mbar_expect_tx(full + 8 * st, (uint32_t)sub_rows(j) * TILE_M * 4);
             const uint32_t dst = smem_u32(rstage0 + st * C::RSTAGE);
-            const CUtensorMap* m0 = j == 0 ? &mR00 : &mR10;
-            const CUtensorMap* m1 = j == 0 ? &mR01 : &mR11;
+            const CUtensorMap* m0 = j == 0 ? &mR00 : (j == 1 ? &mR10 : (j == 2 ? &mR20 : &mR30));
+            const CUtensorMap* m1 = j == 0 ? &mR01 : (j == 1 ? &mR11 : (j == 2 ? &mR21 : &mR31));
             tma_rows(dst, m0, c0, c1, c2, shot * a.nslots + sub_slot(j), full + 8 * st);
             if (sub_n1(j) < sub_rows(j))
               tma_rows(dst + (uint32_t)sub_n1(j) * TILE_M * 4, m1, c0, c1, c2, shot * a.nslots, full + 8 * st);
@@ -715,9 +720,9 @@ cudaError_t launch_ws(const GemmArgs& a, cudaStream_t s) {
   sub.nsub = (a.nlev + KS - 1) / KS;
   const int esize = (ACC == 1 || ACC == 2) ? 2 : 4;
   const int nacc = ACC == 2 ? 2 * a.r : a.r;
-  CUtensorMap mR[2][2], mA, mG;
-  for (int j = 0; j < 2; ++j) {
-    const int jj = j < sub.nsub ? j : 0;  // unused second sub-tile: copies of the first's maps
+  CUtensorMap mR[MAXSUB][2], mA, mG;
+  for (int j = 0; j < MAXSUB; ++j) {
+    const int jj = j < sub.nsub ? j : 0;  // unused sub-tiles: copies of the first's maps
     sub.rows[j] = std::min(KS, a.nlev - KS * jj);
     sub.slot[j] = (a.level0 + KS * jj) % a.nslots;
     sub.n1[j] = std::min(sub.rows[j], a.nslots - sub.slot[j]);
@@ -729,8 +734,9 @@ cudaError_t launch_ws(const GemmArgs& a, cudaStream_t s) {
   if (!encode_field_map(a.L, a.P, (long long)a.nshots * nacc, esize, TILE_M, 1, nacc, &mA) ||
       !encode_field_map(a.L, ACC == 3 ? (const void*)a.G : a.P, a.nshots, 4, TILE_M, 1, 1, &mG))
     return cudaErrorInvalidValue;
-  probe_gemm_ws<KP, ACC><<<grid, WS_THREADS, C::SMEM, s>>>(mR[0][0], mR[0][1], mR[1][0], mR[1][1], mA, mG, a, NP,
-                                                             ntiles, sub);
+  probe_gemm_ws<KP, ACC><<<grid, WS_THREADS, C::SMEM, s>>>(mR[0][0], mR[0][1], mR[1][0], mR[1][1], mR[2][0],
+                                                             mR[2][1], mR[3][0], mR[3][1], mA, mG, a, NP, ntiles,
+                                                             sub);
   return cudaGetLastError();
 }
 
@@ -763,7 +769,7 @@ cudaError_t launch_kp(const GemmArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-int gemm_kpad(int T) { return T <= 32 ? 32 : 64; }
+int gemm_kpad(int T) { return T <= 32 ? 32 : (T <= 64 ? 64 : 128); }
 
 cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
   if (a.nlev <= 0) return cudaSuccess;
@@ -774,12 +780,11 @@ cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
   }();
   cudaError_t e;
   if (a.acc != 0 || (a.r <= GRP && variant == 0)) {  // bf16 storage and dot mode exist on this path only (r <= 32)
-    if (a.nlev <= 32)
-      e = a.acc == 0 ? launch_ws<32, 0>(a, s)
-                     : (a.acc == 1 ? launch_ws<32, 1>(a, s) : (a.acc == 2 ? launch_ws<32, 2>(a, s) : launch_ws<32, 3>(a, s)));
-    else
-      e = a.acc == 0 ? launch_ws<64, 0>(a, s)
-                     : (a.acc == 1 ? launch_ws<64, 1>(a, s) : (a.acc == 2 ? launch_ws<64, 2>(a, s) : launch_ws<64, 3>(a, s)));
+#define TP_WS(KPV) (a.acc == 0 ? launch_ws<KPV, 0>(a, s)                                    \
+                           : (a.acc == 1 ? launch_ws<KPV, 1>(a, s)                         \
+                                         : (a.acc == 2 ? launch_ws<KPV, 2>(a, s) : launch_ws<KPV, 3>(a, s))))
+    e = a.nlev <= 32 ? TP_WS(32) : (a.nlev <= 64 ? TP_WS(64) : TP_WS(128));
+#undef TP_WS
   } else if (a.nlev <= 32) {
     e = a.r <= 16 ? launch_kp<32, 16>(a, s) : (a.r <= 32 ? launch_kp<32, 32>(a, s) : launch_kp<32, 0>(a, s));
   } else {

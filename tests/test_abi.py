@@ -87,6 +87,18 @@ def test_folded_accumulators_halve_the_accumulator_memory(L):
     assert n == 0 and "r <= 32" in native.last_error()
 
 
+def test_window_128_needs_at_most_32_probes(L):
+    w = wl.small_2d(nt=300)
+    g, geo = _grid(w), _geom(w)
+    ok = native.tp_probe(0, 32, 128, 1, None, 0.0)
+    n128 = native.tp_workspace_bytes(native.OP_GRADIENT_PROBED, g, geo, ok)
+    n64 = native.tp_workspace_bytes(native.OP_GRADIENT_PROBED, g, geo, native.tp_probe(0, 32, 64, 1, None, 0.0))
+    assert n128 > n64  # a ring of T + 2 levels
+    bad = native.tp_probe(0, 33, 128, 1, None, 0.0)
+    n = L.tp_workspace_bytes(native.OP_GRADIENT_PROBED, ctypes.byref(g), ctypes.byref(geo), ctypes.byref(bad))
+    assert n == 0 and "T = 128" in native.last_error()
+
+
 @pytest.mark.parametrize("mutate,msg", [
     (lambda g, p: setattr(g, "ndim", 4), "ndim"),
     (lambda g, p: setattr(g, "order", 6), "order"),
