@@ -200,10 +200,15 @@ def test_full_size_3d_grid_truncated_time():
     d = host(p.forward(to_dev(w.vel_true), to_dev(w.wavelet)))
     ref = oracle.batch_forward(w, w.vel_true)
     assert rel_l2(d, ref) <= TRACE_TOL
-    spec = api.ProbeSpec(kind="rademacher", r=32, T=32, seed=w.seed)
-    grad, _ = p.gradient_probed(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs), spec)
     gref, _ = oracle.batch_gradient_probed(w, w.vel0, dobs)
-    assert rel_l2(host(grad), gref) <= GRAD_TOL
+    # every window length at full size: 2 windows of 32, 1 of 64, 1 of 128 (ragged: 45 levels);
+    # two accumulator sets and the single-accumulator form
+    for T in (32, 64, 128):
+        for acc in ("f32", "f32_fold"):
+            spec = api.ProbeSpec(kind="rademacher", r=32, T=T, seed=w.seed, acc=acc)
+            grad, _ = p.gradient_probed(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs), spec)
+            assert rel_l2(host(grad), gref) <= GRAD_TOL, (T, acc, rel_l2(host(grad), gref))
+            p.release()
 
 
 # ------------------------------------------------------------------ the named configurations
