@@ -17,6 +17,8 @@
  * data d[t] = R u[t] (Eq. 2).  The adjoint (Algorithm 1 line 5, f^T) is the
  * exact transpose: lambda[nt] = lambda[nt+1] = 0 and, for j = nt-1..2,
  *     lambda[j] = 2 lambda[j+1] - lambda[j+2] + dt^2 v^2 (L lambda[j+1] + R^T s[j]).
+ * With an absorbing layer (tp_grid.sponge > 0) both steps carry the damping
+ * described at that field; the adjoint stays the exact transpose.
  * m = 1/v^2 is the squared slowness; every gradient returned is dJ/dm of
  * J = 1/2 sum_t ||R u[t] - d_obs[t]||^2 (Eq. 2), i.e. the negative of the
  * update direction delta m that Eq. 3 prints without a sign.
