@@ -704,11 +704,8 @@ cudaError_t launch_ws(const GemmArgs& a, cudaStream_t s) {
   using C = WCfg<KP, ACC>;
   static_assert(C::SMEM <= 227 * 1024, "shared memory of the pipelined GEMM");
   const int NP = std::max(16, (a.r + 15) / 16 * 16);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(probe_gemm_ws<KP, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    attr = true;
-  }
+  const cudaError_t e = smem_limit_once<probe_gemm_ws<KP, ACC>>((int)C::SMEM);
+  if (e != cudaSuccess) return e;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -746,12 +743,12 @@ cudaError_t launch_kp(const GemmArgs& a, cudaStream_t s) {
   int ncols = 32;
   while (ncols < NP) ncols <<= 1;
   const size_t smem = (size_t)2 * TILE_M * KP * 4 + (size_t)2 * NP * KP * 4 + 16;
-  static int regs = 0;
-  if (regs == 0) {
-    cudaFuncSetAttribute(probe_gemm_tf32<KP, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  const cudaError_t e = smem_limit_once<probe_gemm_tf32<KP, PC>>(227 * 1024);
+  if (e != cudaSuccess) return e;
+  static const int regs = [] {  // the same on every device of this architecture
     cudaFuncAttributes fa;
-    regs = cudaFuncGetAttributes(&fa, probe_gemm_tf32<KP, PC>) == cudaSuccess ? std::max(fa.numRegs, 1) : 255;
-  }
+    return cudaFuncGetAttributes(&fa, probe_gemm_tf32<KP, PC>) == cudaSuccess ? std::max(fa.numRegs, 1) : 255;
+  }();
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

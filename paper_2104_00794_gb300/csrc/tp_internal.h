@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace tp {
 
 // Halo width of every padded field in y and z: zero layers around the grid
@@ -201,5 +203,22 @@ void set_last_error(const char* msg);
 // ---------------------------------------------------------------- profiling
 void prof_before(int kind, cudaStream_t s);
 void prof_after(int kind, cudaStream_t s);
+
+// Raises kernel K's dynamic shared-memory limit to `bytes` on the current
+// device, once per device: a function attribute belongs to the device's
+// context, so a process that launches on several devices sets it on each.
+// Thread-safe; devices beyond the first 64 are set on every call.
+template <auto K>
+cudaError_t smem_limit_once(int bytes) {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ULL << dev : 0ULL;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 }  // namespace tp

@@ -413,11 +413,8 @@ namespace {
 template <int R, int MODE, class C, bool DAMP>
 cudaError_t launch_k(const CUtensorMap& mU, const CUtensorMap& m1, const CUtensorMap& m2, const TmaArgs& t,
                      long long blocks, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(sweep3d_tma<R, MODE, C, DAMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    attr = true;
-  }
+  const cudaError_t e = smem_limit_once<sweep3d_tma<R, MODE, C, DAMP>>((int)C::SMEM);
+  if (e != cudaSuccess) return e;
   sweep3d_tma<R, MODE, C, DAMP><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, t);
   return cudaGetLastError();
 }
