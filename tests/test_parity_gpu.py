@@ -171,6 +171,37 @@ def test_tiny_grid_and_coincident_points():
     assert rel_l2(d[0], ref) <= TRACE_TOL
 
 
+@pytest.mark.parametrize("nx,ny,nz", [(5, 3, 2), (9, 1, 6), (131, 2, 1)], ids=["5x3x2", "ny1", "nz1_2xtiles"])
+def test_degenerate_3d_grids(nx, ny, nz):
+    """3-D grids thinner than the stencil radius in y or z, and one plane
+    wider than one 128-point GEMM row: the TMA boxes overhang the fields on
+    every side.  Traces, the full and the probed gradient against the
+    oracle."""
+    nt = 48
+    rng = np.random.default_rng(nx * 100 + ny * 10 + nz)
+    vel_true = (1500.0 + 300.0 * rng.random((nz, ny, nx))).astype(np.float32)
+    vel0 = np.full((nz, ny, nx), 1650.0, np.float32)
+    N = nx * ny * nz
+    src = np.array([[((nz // 2) * ny + ny // 2) * nx + nx // 2]])
+    rec = np.array([[0, src[0, 0] - 1, src[0, 0] + 1, N - 1]])  # two next to the source: 48 steps reach few cells
+    wav = wl.ricker(nt, 1e-3, 30.0).astype(np.float32)[None, :, None]
+    p = api.Problem(3, nx, ny, nz, 10.0, 1e-3, nt, 8, src, rec, vmax=1800.0)
+    g = oracle.make_grid(3, nx, ny, nz, 10.0, 1e-3, nt, 8)
+    d = host(p.forward(to_dev(vel_true), to_dev(wav)))
+    dobs = oracle.forward(g, src[0], rec[0], vel_true, wav[0])
+    assert rel_l2(d[0], dobs) <= TRACE_TOL
+    dobs32 = dobs.astype(np.float32)[None]
+    args = (to_dev(vel0), to_dev(wav), to_dev(dobs32))
+    gf, _ = p.gradient_full(*args)
+    ref_f, _ = oracle.gradient_full(g, src[0], rec[0], vel0, wav[0], dobs32[0])
+    assert np.linalg.norm(ref_f) > 0
+    assert rel_l2(host(gf), ref_f) <= GRAD_TOL
+    Q = oracle.probes("rademacher", nt, 4, 11, 0)
+    ref_p, _ = oracle.gradient_probed(g, src[0], rec[0], vel0, wav[0], dobs32[0], Q, 0.25)
+    gp, _ = p.gradient_probed(*args, api.ProbeSpec(kind="rademacher", r=4, T=32, seed=11))
+    assert rel_l2(host(gp), ref_p) <= GRAD_TOL
+
+
 def test_errors_are_reported():
     w = _w(CASES_2D[1])
     p = problem(w)
