@@ -8,6 +8,7 @@ float32 CUDA tensors of the documented shapes.
 from __future__ import annotations
 
 import dataclasses
+import functools
 from typing import Optional
 
 import torch
@@ -17,6 +18,16 @@ from . import native
 
 def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
+
+
+def _on_device(fn):
+    """Runs a method with its object's device current, so that the current
+    stream and every launch inside the library belong to that device."""
+    @functools.wraps(fn)
+    def run(self, *args, **kw):
+        with torch.cuda.device(self.device):
+            return fn(self, *args, **kw)
+    return run
 
 
 def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
@@ -113,6 +124,7 @@ class Problem:
         self._ws.clear()
 
     # ---------------------------------------------------------------- operators
+    @_on_device
     def forward(self, vel, wavelet, d_out=None):
         vel, wavelet = _f32(vel, self.device), _f32(wavelet, self.device)
         if d_out is None:
@@ -121,6 +133,7 @@ class Problem:
         native.tp_forward(self.grid, self.geom, _ptr(vel), _ptr(wavelet), _ptr(d_out), ws, n, _stream())
         return d_out
 
+    @_on_device
     def adjoint(self, vel, d_in, q_out=None):
         vel, d_in = _f32(vel, self.device), _f32(d_in, self.device)
         if q_out is None:
@@ -129,6 +142,7 @@ class Problem:
         native.tp_adjoint(self.grid, self.geom, _ptr(vel), _ptr(d_in), _ptr(q_out), ws, n, _stream())
         return q_out
 
+    @_on_device
     def gradient_probed(self, vel, wavelet, d_obs, probe: ProbeSpec, grad=None, scalars=None):
         """(grad [dJ/dm], scalars[2] = (misfit, ||grad||)) as device tensors."""
         vel, wavelet, d_obs = _f32(vel, self.device), _f32(wavelet, self.device), _f32(d_obs, self.device)
@@ -141,6 +155,7 @@ class Problem:
                                   _ptr(grad), scalars.data_ptr(), scalars.data_ptr() + 8, ws, n, _stream())
         return grad, scalars
 
+    @_on_device
     def gradient_full(self, vel, wavelet, d_obs, grad=None, scalars=None):
         vel, wavelet, d_obs = _f32(vel, self.device), _f32(wavelet, self.device), _f32(d_obs, self.device)
         if grad is None:
@@ -163,6 +178,7 @@ class Problem:
         off = (-buf.data_ptr()) % 256
         return buf[off:off + n]
 
+    @_on_device
     def probed_forward(self, vel, wavelet, probe: ProbeSpec, state: torch.Tensor, d_out=None):
         """d = F(m; q) and the forward probe accumulators into `state` (Algorithm 1 lines 0-3)."""
         vel, wavelet = _f32(vel, self.device), _f32(wavelet, self.device)
@@ -173,6 +189,7 @@ class Problem:
                                  state.data_ptr(), state.numel(), ws, n, _stream())
         return d_out
 
+    @_on_device
     def probed_backward(self, vel, wavelet, adj_src, probe: ProbeSpec, state: torch.Tensor, wrt_velocity=False,
                         grad=None, gnorm=None):
         """Gradient (dJ/dm, or dJ/dv) from the adjoint source and `state` (Algorithm 1 lines 4-8)."""
@@ -187,6 +204,7 @@ class Problem:
                                   state.numel(), ws, n, _stream())
         return grad, gnorm
 
+    @_on_device
     def probed_image(self, vel, adj_src, probe: ProbeSpec, state: torch.Tensor, cond: str = "gradient",
                      image=None):
         """Imaging condition on the probed fields (Eq. 5): scale * sum_i <D P_i, D V_i>
@@ -201,6 +219,7 @@ class Problem:
                                _stream())
         return image
 
+    @_on_device
     def qr_probes(self, d_obs, r: int, seed: int = 2104, kind: str = "rademacher") -> torch.Tensor:
         """Range-finding probes of Eq. 6, [nshots, nt, r], from the observed
         records; use them as ProbeSpec(kind="user", Z_user=Q, r=r)."""
@@ -215,12 +234,14 @@ class Problem:
         native.tp_workspace_status(ws, n, _stream())
         return Q
 
+    @_on_device
     def probes(self, probe: ProbeSpec, shot: int = 0, nt: Optional[int] = None):
         nt = self.nt if nt is None else nt
         Z = torch.empty((nt, probe.r), dtype=torch.float32, device=self.device)
         native.tp_probes(probe.to_c(), nt, shot, _ptr(Z), _stream())
         return Z
 
+    @_on_device
     def status(self, op: int):
         """Raises if a bounded device-side wait of the last `op` call timed out."""
         buf = self._ws.get(op)
@@ -245,6 +266,11 @@ class GraphedGradient:
     (the spec's seed); use a new GraphedGradient for new probes."""
 
     def __init__(self, problem: Problem, probe: Optional[ProbeSpec] = None, full: bool = False):
+        self.device = problem.device
+        with torch.cuda.device(self.device):
+            self._capture(problem, probe, full)
+
+    def _capture(self, problem: Problem, probe: Optional[ProbeSpec], full: bool):
         if not problem.grid.vmax > 0.0:
             raise ValueError("a graphed gradient needs the grid's vmax (no host synchronisation inside the call)")
         if not full and probe is None:
@@ -279,6 +305,7 @@ class GraphedGradient:
             self.problem.gradient_probed(self.vel, self.wavelet, self.d_obs, self.probe, grad=self.grad,
                                          scalars=self.scalars)
 
+    @_on_device
     def __call__(self, vel, wavelet, d_obs, grad_out: Optional[torch.Tensor] = None,
                  scalars_out: Optional[torch.Tensor] = None):
         self.vel.copy_(vel, non_blocking=True)

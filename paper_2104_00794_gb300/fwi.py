@@ -120,8 +120,9 @@ def invert(problem, vel0, wavelet, d_obs, vmin: float, vmax: float, iters: int, 
     def misfit(m):
         d = problem.forward(vel_of(m), wavelet)
         # J = 1/2 |d - d_obs|^2 in fp64 by the library's reduction kernels
-        native.tp_misfit_noalloc(d.data_ptr(), d_obs.data_ptr(), d.numel(), J.data_ptr(),
-                                 torch.cuda.current_stream().cuda_stream)
+        with torch.cuda.device(dev):
+            native.tp_misfit_noalloc(d.data_ptr(), d_obs.data_ptr(), d.numel(), J.data_ptr(),
+                                     torch.cuda.current_stream().cuda_stream)
         return float(J.item())
 
     def fg(m):
