@@ -710,7 +710,10 @@ cudaError_t launch_ws(const GemmArgs& a, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (long long)a.L.nz * a.L.ny * ((a.L.nx + TILE_M - 1) / TILE_M);
-  const long long grid_x = std::min<long long>(ntiles, (long long)sms);  // one CTA per SM
+  // one CTA per SM, the SMs shared among the shots: each persistent CTA then
+  // loops over many tiles of its shot (a full SM count per shot made one short
+  // wave of CTAs per shot, dominated by pipeline fill and drain)
+  const long long grid_x = std::min<long long>(ntiles, std::max<long long>(1, (long long)sms / a.nshots));
   dim3 grid((unsigned)grid_x, a.nshots);
   // the window's sub-tiles of KS levels, each split where the ring wraps
   SubTiles sub{};
@@ -758,7 +761,7 @@ cudaError_t launch_kp(const GemmArgs& a, cudaStream_t s) {
   const int by_tmem = 512 / ncols;
   const int occ = std::max(1, std::min(std::min(by_regs, by_smem), std::min(by_tmem, 8)));
   const long long ntiles = (long long)a.L.nz * a.L.ny * ((a.L.nx + TILE_M - 1) / TILE_M);
-  const long long grid_x = std::min<long long>(ntiles, (long long)sms * occ);
+  const long long grid_x = std::min<long long>(ntiles, std::max<long long>(1, (long long)sms * occ / a.nshots));
   dim3 grid((unsigned)grid_x, a.nshots);
   probe_gemm_tf32<KP, PC><<<grid, TILE_M, smem, s>>>(a, NP, ncols, ntiles);
   return cudaGetLastError();
