@@ -257,25 +257,27 @@ sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) 
   }
 }
 
-int g_num_sms = 0;
-
+// SM count of the current device, cached per device (thread-safe)
 int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int n = dev >= 0 && dev < 64 ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (n <= 0) {
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+    if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
   }
-  return g_num_sms;
+  return n;
 }
 
 template <int R, int MODE>
 cudaError_t launch3d(const Layout& L, const Weights& W, const PlainArgs& a, cudaStream_t s) {
-  static int occ = 0;
-  if (occ == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep3d<R, MODE, false>, T3X * T3Y, 0);
-    if (occ <= 0) occ = 1;
-  }
+  static const int occ = [] {  // the same on every device of this architecture
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, sweep3d<R, MODE, false>, T3X * T3Y, 0);
+    return o > 0 ? o : 1;
+  }();
   const int gx = (L.nx + 4 * T3X - 1) / (4 * T3X), gy = (L.ny + T3Y - 1) / T3Y;
   const long long tiles = (long long)gx * gy * a.nshots;
   const long long target = 2LL * occ * num_sms();
