@@ -432,7 +432,7 @@ def main():
         h2d = h_vel.numel() * 4 + h_wav.numel() * 4 + h_dobs.numel() * 4
         e2e = {"value": pts * world / (ems * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_step": ems,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h_grad.numel() * 4 + 16),
-               "api": "api.GraphedGradient (captured once, replayed per call)"}
+               "api": "api.GraphedGradient (captured once, replayed per call; d_obs uploaded beside the forward half)"}
         del gg
         p.release()
 

@@ -203,6 +203,21 @@ tp_status tp_probed_backward(const tp_grid* grid, const tp_geom* geom, const tp_
                              int wrt_velocity, float* grad, double* gnorm, void* state,
                              size_t state_bytes, void* ws, size_t ws_bytes, void* stream);
 
+/* The data residual and misfit between the halves (Eq. 2): d becomes the
+ * residual d - d_obs in place, and J = 1/2 sum_i (d[i] - d_obs[i])^2 is
+ * reduced in fp64 in a fixed order and written to the DEVICE double *misfit.
+ * With d = the d_out of tp_probed_forward, the residual is the adj_src of
+ * tp_probed_backward, and the three calls give bit for bit what
+ * tp_gradient_probed gives (same kernels, same order): a caller can then
+ * upload d_obs while the forward half runs.  d, d_obs: device float arrays
+ * of n samples (any layout, e.g. [nshots][nt][nrec]); ws: caller-owned device
+ * workspace of tp_residual_workspace_bytes() bytes, 256-byte aligned (fp64
+ * partial sums).  Errors: TP_ERR_ARG (NULL pointer, n < 1, misaligned ws),
+ * TP_ERR_NOMEM (ws too small), TP_ERR_CUDA (launch failed). */
+size_t tp_residual_workspace_bytes(void);
+tp_status tp_residual(float* d, const float* d_obs, int64_t n, double* misfit, void* ws, size_t ws_bytes,
+                      void* stream);
+
 /* Imaging conditions on the probed wavefields (§Imaging conditions, Eq. 5:
  * a linear operator D that acts on space only commutes with probing,
  * Q^T (D u) = D (Q^T u)).  tp_probed_image applies D to the r probed fields

@@ -253,17 +253,21 @@ class Problem:
 
 
 class GraphedGradient:
-    """One Problem's gradient captured once as a CUDA graph and replayed per call.
+    """One Problem's gradient captured once as CUDA graphs and replayed per call.
 
     Every kernel of the gradient is enqueued by the library without host
     synchronisation (given the grid's vmax), so the whole call -- a few
-    thousand kernels for nt = 2000 -- is captured once and launched as one
-    graph.  Inputs (host tensors, preferably pinned, or device tensors) are
-    copied into the graph's static device buffers, the graph is replayed on
-    the current stream, and the gradient and (misfit, |g|) are copied into
-    the caller's outputs when given (else the static device tensors are
-    returned, overwritten by the next call).  The probes are fixed at capture
-    (the spec's seed); use a new GraphedGradient for new probes."""
+    thousand kernels for nt = 2000 -- is captured once and launched as
+    graphs.  Inputs (host tensors, preferably pinned, or device tensors) are
+    copied into static device buffers, the graphs are replayed on the current
+    stream, and the gradient and (misfit, |g|) are copied into the caller's
+    outputs when given (else the static device tensors are returned,
+    overwritten by the next call).  The probed gradient runs as its two
+    halves (tp_probed_forward; tp_residual and tp_probed_backward), which give
+    tp_gradient_probed's result bit for bit; d_obs is first read by the
+    residual, so its upload runs on a second stream beside the forward half.
+    The probes are fixed at capture (the spec's seed); use a new
+    GraphedGradient for new probes."""
 
     def __init__(self, problem: Problem, probe: Optional[ProbeSpec] = None, full: bool = False):
         self.device = problem.device
@@ -284,34 +288,64 @@ class GraphedGradient:
         self.d_obs = torch.zeros((problem.nshots, problem.nt, problem.geom.nrec), dtype=torch.float32, device=dev)
         self.grad = torch.empty(shape, dtype=torch.float32, device=dev)
         self.scalars = torch.empty(2, dtype=torch.float64, device=dev)
-        self._run()  # allocates the workspace outside the capture
-        # the graph keeps raw pointers into the workspace: hold it, so that
-        # problem.release() cannot free it under the graph
-        op = native.OP_GRADIENT_FULL if full else native.OP_GRADIENT_PROBED
-        self._ws = problem._ws[op]
+        if full:
+            parts = [self._full]
+        else:
+            self.state = problem.new_state(probe)
+            self.d_syn = torch.empty_like(self.d_obs)
+            n = native.tp_residual_workspace_bytes()
+            self._rbuf = torch.empty(n + 256, dtype=torch.uint8, device=dev)
+            self._rws = (self._rbuf.data_ptr() + (-self._rbuf.data_ptr()) % 256, n)
+            parts = [self._forward_half, self._backward_half]
+        for run in parts:  # allocates the workspaces outside the capture
+            run()
+        # the graphs keep raw pointers into the workspaces: hold them, so that
+        # problem.release() cannot free them under the graphs
+        ops = [native.OP_GRADIENT_FULL] if full else [native.OP_PROBED_FORWARD, native.OP_PROBED_BACKWARD]
+        self._ws = [problem._ws[op] for op in ops]
         torch.cuda.synchronize(dev)
         side = torch.cuda.Stream(device=dev)
+        self.graphs = []
         with torch.cuda.stream(side):
-            self.graph = torch.cuda.CUDAGraph()
-            self.graph.capture_begin()
-            self._run()
-            self.graph.capture_end()
+            for run in parts:
+                gr = torch.cuda.CUDAGraph()
+                gr.capture_begin()
+                run()
+                gr.capture_end()
+                self.graphs.append(gr)
         torch.cuda.synchronize(dev)
+        self._upload = torch.cuda.Stream(device=dev)
 
-    def _run(self):
-        if self.full:
-            self.problem.gradient_full(self.vel, self.wavelet, self.d_obs, grad=self.grad, scalars=self.scalars)
-        else:
-            self.problem.gradient_probed(self.vel, self.wavelet, self.d_obs, self.probe, grad=self.grad,
-                                         scalars=self.scalars)
+    def _full(self):
+        self.problem.gradient_full(self.vel, self.wavelet, self.d_obs, grad=self.grad, scalars=self.scalars)
+
+    def _forward_half(self):
+        self.problem.probed_forward(self.vel, self.wavelet, self.probe, self.state, d_out=self.d_syn)
+
+    def _backward_half(self):
+        native.tp_residual(self.d_syn.data_ptr(), self.d_obs.data_ptr(), self.d_syn.numel(),
+                           self.scalars.data_ptr(), self._rws[0], self._rws[1], _stream())
+        self.problem.probed_backward(self.vel, self.wavelet, self.d_syn, self.probe, self.state, grad=self.grad,
+                                     gnorm=self.scalars[1:])
 
     @_on_device
     def __call__(self, vel, wavelet, d_obs, grad_out: Optional[torch.Tensor] = None,
                  scalars_out: Optional[torch.Tensor] = None):
+        main = torch.cuda.current_stream()
         self.vel.copy_(vel, non_blocking=True)
         self.wavelet.copy_(wavelet, non_blocking=True)
-        self.d_obs.copy_(d_obs, non_blocking=True)
-        self.graph.replay()
+        if self.full:
+            self.d_obs.copy_(d_obs, non_blocking=True)
+            self.graphs[0].replay()
+        else:
+            self._upload.wait_stream(main)  # the previous call's backward half has read d_obs
+            self.graphs[0].replay()
+            with torch.cuda.stream(self._upload):  # beside the forward half
+                self.d_obs.copy_(d_obs, non_blocking=True)
+                if d_obs.is_cuda:
+                    d_obs.record_stream(self._upload)
+            main.wait_stream(self._upload)
+            self.graphs[1].replay()
         if grad_out is not None:
             grad_out.copy_(self.grad, non_blocking=True)
         if scalars_out is not None:

@@ -729,6 +729,26 @@ tp_status tp_probed_backward(const tp_grid* grid, const tp_geom* geom, const tp_
                               reinterpret_cast<const float*>(st + P.s_Q), st + P.s_P);
 }
 
+size_t tp_residual_workspace_bytes(void) { return NBLK * sizeof(double) + SCAL_BYTES; }
+
+tp_status tp_residual(float* d, const float* d_obs, int64_t n, double* misfit, void* ws, size_t ws_bytes,
+                      void* stream) {
+  if (!d || !d_obs || !misfit) return fail(TP_ERR_ARG, "d/d_obs/misfit is NULL");
+  if (n < 1) return fail(TP_ERR_ARG, "n must be >= 1");
+  if (!ws) return fail(TP_ERR_ARG, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(TP_ERR_ARG, "workspace must be 256-byte aligned");
+  if (ws_bytes < tp_residual_workspace_bytes())
+    return fail(TP_ERR_NOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, tp_residual_workspace_bytes());
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* part = static_cast<double*>(ws);
+  Scal* sc = reinterpret_cast<Scal*>(static_cast<char*>(ws) + NBLK * sizeof(double));
+  TRY(cudaMemsetAsync(sc, 0, SCAL_BYTES, st));
+  // the reduction of the fused gradient call (misfit_and_residual), on the caller's buffers
+  TRY(launch_residual(d, d_obs, (long long)n, part, NBLK, st));
+  TRY(launch_finalize_sum(part, NBLK, 0.5, misfit, 0, &sc->err, st));
+  return TP_OK;
+}
+
 tp_status tp_probed_image(const tp_grid* grid, const tp_geom* geom, const tp_probe* probe, const float* vel,
                           const float* adj_src, int cond, float* image, const void* state, size_t state_bytes,
                           void* ws, size_t ws_bytes, void* stream) {

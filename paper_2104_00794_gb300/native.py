@@ -80,6 +80,9 @@ def lib():
         L.tp_probed_forward.argtypes = [G, E, Pr, vp, vp, vp, vp, sz, vp, sz, vp]
         L.tp_probed_backward.argtypes = [G, E, Pr, vp, vp, vp, i32, vp, vp, vp, sz, vp, sz, vp]
         L.tp_probed_image.argtypes = [G, E, Pr, vp, vp, i32, vp, vp, sz, vp, sz, vp]
+        L.tp_residual_workspace_bytes.argtypes = []
+        L.tp_residual_workspace_bytes.restype = sz
+        L.tp_residual.argtypes = [vp, vp, ctypes.c_int64, vp, vp, sz, vp]
         L.tp_last_error.restype = ctypes.c_char_p
         L.tp_profile_begin.argtypes = [i32]
         L.tp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -87,7 +90,7 @@ def lib():
         L.tp_kernel_name.restype = ctypes.c_char_p
         for f in ("tp_forward", "tp_adjoint", "tp_gradient_probed", "tp_gradient_full", "tp_probes",
                   "tp_workspace_status", "tp_profile_begin", "tp_profile_end", "tp_misfit_noalloc",
-                  "tp_probed_forward", "tp_probed_backward", "tp_qr_probes", "tp_probed_image"):
+                  "tp_probed_forward", "tp_probed_backward", "tp_qr_probes", "tp_probed_image", "tp_residual"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
         return L
@@ -166,6 +169,16 @@ def tp_qr_probes(probe, nt, nrec, nshots, d_obs, Q, ws, ws_bytes, stream):
 
 def tp_probes(probe, nt, shot, Z, stream):
     _check(lib().tp_probes(ctypes.byref(probe), nt, shot, Z, stream))
+
+
+def tp_residual_workspace_bytes() -> int:
+    return int(lib().tp_residual_workspace_bytes())
+
+
+def tp_residual(d, d_obs, n, misfit, ws, ws_bytes, stream):
+    """d -= d_obs in place (the adjoint source) and J = 1/2 sum (d - d_obs)^2
+    into the device double at `misfit` (Eq. 2, the fused call's reduction)."""
+    _check(lib().tp_residual(d, d_obs, n, misfit, ws, ws_bytes, stream))
 
 
 def tp_misfit_noalloc(d_syn, d_obs, n, misfit, stream):

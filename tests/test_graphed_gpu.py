@@ -2,12 +2,14 @@
 inputs.  Every kernel is deterministic (fixed work split, fixed-order
 reductions), so a replay must equal the eager call bit for bit, for host
 (pinned) and device inputs, for consecutive calls with different models, and
-for the probed and the full-storage gradient."""
+for the probed and the full-storage gradient.  The probed form runs as its
+halves with tp_residual between them (d_obs uploaded beside the forward
+half), which must give tp_gradient_probed's result bit for bit."""
 import numpy as np
 import pytest
 import torch
 
-from paper_2104_00794_gb300 import api
+from paper_2104_00794_gb300 import api, native
 from paper_2104_00794_gb300 import workloads as wl
 from parity_util import oracle_dobs, problem, to_dev
 
@@ -67,3 +69,28 @@ def test_graphed_gradient_needs_vmax():
     p = api.Problem.from_workload(w, vmax=0.0)
     with pytest.raises(ValueError, match="vmax"):
         api.GraphedGradient(p, api.ProbeSpec(r=4))
+
+
+def test_residual_entry_point():
+    """tp_residual (Eq. 2): d - d_obs in place, 1/2 |d - d_obs|^2 in fp64."""
+    rng = np.random.default_rng(5)
+    n = 3 * 1000 * 601 + 7
+    d_h = rng.standard_normal(n).astype(np.float32)
+    o_h = rng.standard_normal(n).astype(np.float32)
+    d, o = to_dev(d_h), to_dev(o_h)
+    J = torch.zeros(1, dtype=torch.float64, device="cuda")
+    nb = native.tp_residual_workspace_bytes()
+    buf = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    ws = buf.data_ptr() + (-buf.data_ptr()) % 256
+    s = torch.cuda.current_stream().cuda_stream
+    native.tp_residual(d.data_ptr(), o.data_ptr(), n, J.data_ptr(), ws, nb, s)
+    res = d_h - o_h  # fp32, exact IEEE subtraction on both sides
+    assert np.array_equal(d.cpu().numpy(), res)
+    ref = 0.5 * float(np.sum(res.astype(np.float64) ** 2))
+    assert abs(float(J.item()) - ref) <= 1e-12 * ref
+    with pytest.raises(native.TprobeError) as e:
+        native.tp_residual(d.data_ptr(), o.data_ptr(), n, J.data_ptr(), ws, nb - 8, s)
+    assert e.value.status == native.TP_ERR_NOMEM
+    with pytest.raises(native.TprobeError) as e:
+        native.tp_residual(d.data_ptr(), o.data_ptr(), 0, J.data_ptr(), ws, nb, s)
+    assert e.value.status == native.TP_ERR_ARG
