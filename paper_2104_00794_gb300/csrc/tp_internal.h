@@ -44,9 +44,10 @@ struct Layout {
 Layout make_layout(int ndim, int nx, int ny, int nz);
 
 // Centred second-derivative weights w[0..R] (Fornberg 1988) for order 2R.
-// The sweeps use w[1..R] in the difference form sum_k w_k (u[+k] + u[-k] - 2u)
-// per axis, which equals w[0] u + sum_k w_k (u[+k] + u[-k]) because
-// w[0] = -2 sum_k w_k, and stays exact for constants in fp32.
+// The sweeps use w[1..R] in the centred form sum_k w_k (sum of the 2 ndim
+// neighbours at distance k - 2 ndim u), which equals ndim w[0] u + sum_k w_k
+// (neighbours) because w[0] = -2 sum_k w_k, and leaves no zero-order term from
+// the fp32 rounding of w[0].
 struct Weights {
   float w[5];
   int R;
@@ -92,7 +93,7 @@ struct FieldRef {
 // MODE_INC  : w' = p1 + p2 * S(src), out = src + w', and w' is stored to out2
 //             (the increment form: p1 = out2 = the increment u[t] - u[t-1])
 // MODE_IMAGE: out = p2 + p1 * S(src)  (out may alias p2: accumulate)
-// S(.) = the stencil sum without 1/h^2, in the difference form.  `out` is the shot-0 field,
+// S(.) = the stencil sum without 1/h^2, in the centred form.  `out` is the shot-0 field,
 // out_ss the per-shot stride in floats.
 struct StencilArgs {
   FieldRef src, p1, p2;

@@ -135,16 +135,15 @@ sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
 
     const float4 xl = sm[ty + R][tx], xc = sm[ty + R][tx + 1], xr = sm[ty + R][tx + 2];
     const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-    float s[4] = {0.f, 0.f, 0.f, 0.f};  // difference form (see tp_sweep3d_tma.cu)
+    float s[4] = {0.f, 0.f, 0.f, 0.f};  // centred form (see tp_sweep3d_tma.cu)
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
       const float4 yp = sm[ty + R + k][tx + 1], ym = sm[ty + R - k][tx + 1];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const float c = v[4 + p];
-        const float t = ((v[4 + p + k] - c) + (v[4 + p - k] - c)) + ((comp(yp, p) - c) + (comp(ym, p) - c)) +
-                        ((comp(q[R + k], p) - c) + (comp(q[R - k], p) - c));
-        s[p] = fmaf(W.w[k], t, s[p]);
+        const float nb = ((v[4 + p + k] + v[4 + p - k]) + (comp(yp, p) + comp(ym, p))) +
+                         (comp(q[R + k], p) + comp(q[R - k], p));
+        s[p] = fmaf(W.w[k], fmaf(-6.0f, v[4 + p], nb), s[p]);
       }
     }
     float res[4], inc[4];
@@ -218,12 +217,11 @@ sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) 
     __syncwarp();
     const float4 xl = sm[wi][lane], xc = sm[wi][lane + 1], xr = sm[wi][lane + 2];
     const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-    // difference form (annihilates constants whatever the weight rounding), two
-    // points per packed fp32x2 instruction: each lane is the scalar operation in
-    // the same order (u[+k] - u as fma(u, -1, u[+k]), exact product), so the
-    // result is bit-identical to the scalar loop
+    // centred form (see tp_sweep3d_tma.cu): sum_k w_k (neighbour sum - 4u), the -4u
+    // folded into one FMA; two points per packed fp32x2 instruction, each lane the
+    // scalar operation in the same order
     float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    const float2 neg1 = make_float2(-1.f, -1.f);
+    const float2 m4 = make_float2(-4.f, -4.f);
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
       const float4 zp = q[R + k], zm = q[R - k];
@@ -232,11 +230,10 @@ sweep2d(Layout L, Weights W, PlainArgs a, int bz, int nzc, int nxt, int nwarps) 
       for (int h = 0; h < 2; ++h) {
         const int p = 2 * h;
         const float2 c = make_float2(v[4 + p], v[5 + p]);
-        const float2 dxp = __ffma2_rn(c, neg1, make_float2(v[4 + p + k], v[5 + p + k]));
-        const float2 dxm = __ffma2_rn(c, neg1, make_float2(v[4 + p - k], v[5 + p - k]));
-        const float2 dzp = __ffma2_rn(c, neg1, h ? make_float2(zp.z, zp.w) : make_float2(zp.x, zp.y));
-        const float2 dzm = __ffma2_rn(c, neg1, h ? make_float2(zm.z, zm.w) : make_float2(zm.x, zm.y));
-        s2[h] = __ffma2_rn(wk, __fadd2_rn(__fadd2_rn(dxp, dxm), __fadd2_rn(dzp, dzm)), s2[h]);
+        const float2 xs = __fadd2_rn(make_float2(v[4 + p + k], v[5 + p + k]), make_float2(v[4 + p - k], v[5 + p - k]));
+        const float2 zs = __fadd2_rn(h ? make_float2(zp.z, zp.w) : make_float2(zp.x, zp.y),
+                                     h ? make_float2(zm.z, zm.w) : make_float2(zm.x, zm.y));
+        s2[h] = __ffma2_rn(wk, __ffma2_rn(m4, c, __fadd2_rn(xs, zs)), s2[h]);
       }
     }
     const float s4[4] = {s2[0].x, s2[0].y, s2[1].x, s2[1].y};
