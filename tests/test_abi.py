@@ -139,6 +139,17 @@ def test_null_geometry_and_counts_rejected(L):
     assert st == native.TP_ERR_NOMEM and "needed" in native.last_error()
 
 
+def test_residual_arguments_checked_before_the_device(L):
+    nb = L.tp_residual_workspace_bytes()
+    assert nb >= 1024 * 8  # fp64 partial sums
+    # NULL pointers, n < 1, misaligned or small workspaces fail before any CUDA call
+    assert L.tp_residual(None, 0x1000, 10, 0x1000, 0x1000, nb, None) == native.TP_ERR_ARG
+    assert L.tp_residual(0x1000, 0x1000, 0, 0x1000, 0x1000, nb, None) == native.TP_ERR_ARG
+    assert L.tp_residual(0x1000, 0x1000, 10, 0x1000, 0x1008, nb, None) == native.TP_ERR_ARG
+    assert "aligned" in native.last_error()
+    assert L.tp_residual(0x1000, 0x1000, 10, 0x1000, 0x1000, nb - 8, None) == native.TP_ERR_NOMEM
+
+
 def test_kernel_names(L):
     names = [L.tp_kernel_name(k).decode() for k in range(native.KERNEL_KINDS)]
     assert names[0] == "stencil_step" and "probe_gemm_tcgen05" in names
