@@ -3,7 +3,7 @@
 // Algorithm 1 accumulates, at every time level k, ubar[x,:] += Q[k,:] * w_k[x]
 // (lines 2 and 6).  Over a window of T levels this is the dense contraction
 //     P[x, i] += sum_{k in window} W[x, k] * Q[k, i],
-// M = grid points (10^4 .. 2*10^7), K = T (32/64), N = r (4..256), with W the
+// M = grid points (10^4 .. 2*10^7), K = T (32/64/128), N = r (4..256), with W the
 // T ring snapshots that the stencil sweeps already wrote.  Every tile of 128
 // points splits its fp32 snapshots into tf32 hi + lo parts in shared memory
 // (K-major, no-swizzle core-matrix layout: 8 rows x 16 B core matrices), one
@@ -17,8 +17,9 @@
 // Two kernels:
 //   * probe_gemm_ws (r <= 32, every accumulator storage and the dot mode of
 //     the single-accumulator adjoint): a warp-specialised pipeline with 4-D
-//     TMA tensor copies and stores, one CTA per SM; described where it is
-//     defined below.  It runs at the HBM roofline.
+//     TMA tensor copies and stores, one CTA per SM (the SMs shared among the
+//     shots of a batch); described where it is defined below.  It runs at the
+//     HBM roofline.
 //   * probe_gemm_tf32 (r > 32, e.g. identity probes with r = nt in tests):
 //     128 threads per tile load the snapshots through registers, one thread
 //     issues the MMAs, all threads drain TMEM into P.
