@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--nt", type=int, default=2000)
     ap.add_argument("--r", type=int, default=32)
     ap.add_argument("--T", type=int, default=32)
-    ap.add_argument("--form", default="levels", choices=["levels", "increment"], help="fp32 time-stepping form")
+    ap.add_argument("--form", default="auto", choices=["auto", "levels", "increment", "compensated"],
+                    help="fp32 time-stepping form (auto: compensated forward for 2-D grids that fit one cluster)")
     ap.add_argument("--acc", default="f32", choices=["f32", "bf16", "bf16_kahan", "f32_fold"],
                     help="probe accumulator storage of the headline gradient")
     ap.add_argument("--no-fold", action="store_true", help="skip the single-accumulator comparison")
@@ -360,7 +361,9 @@ def main():
     # ---- roofline of the dominant kernel (leapfrog stencil step)
     hbm_peak, _, peak_kind = measured_peaks()
     st = kern["stencil_step"]
-    avg_stencil_ms = st["ms"] / max(st["launches"], 1)
+    # time per time step (a 2-D launch on the cluster path runs many steps)
+    steps_per_grad = 2 * (w.nt - 2)
+    avg_stencil_ms = st["ms"] / (args.steps * steps_per_grad)
     stencil_bytes = STENCIL_BYTES_PER_POINT * w.N * w.nshots
     achieved = stencil_bytes / (avg_stencil_ms * 1e-3) / 1e9
     key = f"{w.ndim}d {w.nx}^3 r{w.r} T{w.T}" if (w.ndim == 3 and w.nx == w.ny == w.nz) else w.name
@@ -477,8 +480,9 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"kernel": "stencil_step", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_kind,
-                         "traffic": traffic, "bytes_per_launch_algorithmic": stencil_bytes,
-                         "avg_launch_ms": avg_stencil_ms, "launches": st["launches"]},
+                         "traffic": traffic, "bytes_per_step_algorithmic": stencil_bytes,
+                         "avg_step_ms": avg_stencil_ms, "launches": st["launches"],
+                         "steps": args.steps * steps_per_grad, "form": p.form},
             "probe_gemm": {"avg_launch_ms": avg_gemm_ms, "launches": gm["launches"],
                            "bytes_per_launch_algorithmic": gemm_bytes,
                            "achieved_gbs": gemm_bytes / (avg_gemm_ms * 1e-3) / 1e9 if gm["launches"] else None,

@@ -26,7 +26,9 @@
  * Conventions for every entry point:
  *   - All array arguments are DEVICE pointers owned by the caller, unless a
  *     parameter says "host".  Nothing is allocated on the hot path: scratch
- *     space is the caller's workspace, sized by tp_workspace_bytes().
+ *     space is the caller's workspace, sized by tp_workspace_bytes(); the one
+ *     exception is tp_misfit_noalloc, whose scratch is a fixed 32 KiB array
+ *     inside the library that all of its calls share.
  *   - Work is enqueued asynchronously on `stream` (a cudaStream_t, NULL for
  *     the legacy default stream); results are ready once the stream is.
  *   - float = IEEE fp32; the wavefields are fp32 and the misfit / gradient
@@ -103,7 +105,15 @@ typedef struct {
                   (u[t], u[t-1]); TP_FORM_INCREMENT keeps (u[t], u[t] - u[t-1]),
                   so that the rounding of u is integrated once instead of
                   twice (more accurate over thousands of steps, one more
-                  4-byte write per point and step) */
+                  4-byte write per point and step); TP_FORM_COMPENSATED steps
+                  the forward wavefield as a double-float u + e (fp32 level,
+                  bf16 low part) with error-free sums, so that the rounding of
+                  the stored levels is carried instead of lost (the probed
+                  gradient applies the Laplacian to the probed forward field,
+                  which amplifies that rounding); the adjoint keeps the levels
+                  form.  TP_FORM_COMPENSATED needs a 2-D grid without an
+                  absorbing layer whose shot fits one thread-block cluster
+                  (tp_form_supported) */
   int sponge;  /* absorbing layer (not in the paper): width in cells on every
                   face but the top z = 0, which stays the zero-pressure free
                   surface; 0: none (the undamped scheme, bit for bit).  The
@@ -115,7 +125,7 @@ typedef struct {
   float sponge_eta; /* peak damping eta_max [1/s], >= 0 */
 } tp_grid;
 
-typedef enum { TP_FORM_LEVELS = 0, TP_FORM_INCREMENT = 1 } tp_form;
+typedef enum { TP_FORM_LEVELS = 0, TP_FORM_INCREMENT = 1, TP_FORM_COMPENSATED = 2 } tp_form;
 
 /* Acquisition of a batch of independent shots sharing one model.  S^T and R
  * of Eq. 2 / Algorithm 1: on-grid point sources and receivers. */
@@ -139,6 +149,11 @@ typedef struct {
                           random probes (Eq. 1), 1 for IDENTITY and USER */
   int acc;             /* tp_acc storage of the accumulators; all but F32 need r <= 32 */
 } tp_probe;
+
+/* TP_OK if this library can run `grid` (its form in particular) for batches
+ * shaped like `geom` (only the counts of geom are read), else TP_ERR_ARG with
+ * the reason in tp_last_error().  No device work. */
+tp_status tp_form_supported(const tp_grid* grid, const tp_geom* geom);
 
 /* Bytes of device workspace that `op` needs (0 on invalid arguments; see
  * tp_last_error).  `probe` is read only for the probed ops.  The workspace
@@ -266,9 +281,12 @@ tp_status tp_probes(const tp_probe* probe, int nt, int shot, float* Z, void* str
  * bring) is not acceptable.  Its scratch (one fp64 partial per 65536 samples)
  * is a fixed 32 KiB array inside the library, held on every GPU that loads the
  * library until the process exits; so n may be at most 268,435,456 samples
- * (TP_ERR_ARG beyond).  The first call on a device looks the array up on that
- * device (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Calls share the array: calls that overlap on the GPU race and must
+ * (TP_ERR_ARG beyond).  Each call made outside stream capture looks the
+ * array up on the current device (cudaGetSymbolAddress), so a device reset
+ * between calls is harmless; a call made during capture uses the address of
+ * the last call outside capture on that device, so make the first call on a
+ * device before any capture, and none across a device reset during capture.
+ * Calls share the array: calls that overlap on the GPU race and must
  * be ordered by the caller.  d_syn, d_obs: device float arrays of n samples
  * (any layout, e.g. [nshots][nt][nrec]).  Errors: TP_ERR_ARG (NULL pointer,
  * n < 1 or too large), TP_ERR_CUDA (lookup or launch failed). */
@@ -278,6 +296,19 @@ tp_status tp_misfit_noalloc(const float* d_syn, const float* d_obs, int64_t n, d
  * the last call on this workspace gave up (TP_ERR_TIMEOUT) or not (TP_OK);
  * clears the flag. */
 tp_status tp_workspace_status(void* ws, size_t ws_bytes, void* stream);
+
+/* Sets the spin limit, in SM clock cycles, of the bounded device-side waits
+ * between the roles of the pipelined kernels (the 3-D sweep's copy producer
+ * and its consumers) for every launch that follows, process-wide; 0 restores
+ * the default (2e9 cycles, about one second).  Waits by which a kernel that
+ * gives up first lets its own copies land keep the default, so a kernel always
+ * exits with nothing in flight.  A limit shorter than a copy's latency makes
+ * the waits give up: the calls launched with it set the flag that
+ * tp_workspace_status reports as TP_ERR_TIMEOUT, their misfit and gradient
+ * norm read NaN, and their other results are invalid.  The paper has no
+ * counterpart: this exists to exercise the timeout path.  Errors: TP_ERR_ARG
+ * (cycles < 0). */
+tp_status tp_set_wait_limit(int64_t cycles);
 
 /* Thread-local message of the last error on the calling thread ("" if none). */
 const char* tp_last_error(void);

@@ -67,7 +67,11 @@ class Problem:
     """A batch of shots on one model grid, with device-resident geometry."""
 
     def __init__(self, ndim, nx, ny, nz, h, dt, nt, order, src, rec, vmax: float = 0.0, device="cuda",
-                 form: str = "levels", sponge: int = 0, sponge_eta: float = 0.0):
+                 form: str = "auto", sponge: int = 0, sponge_eta: float = 0.0):
+        """form: the fp32 time stepping (tp_grid.form).  "auto" takes the
+        compensated forward where the library supports it (2-D grids without an
+        absorbing layer whose shot fits one thread-block cluster) and the
+        levels form elsewhere."""
         self.device = torch.device(device)
         self.src = torch.as_tensor(src, dtype=torch.int64, device=self.device).contiguous()
         self.rec = torch.as_tensor(rec, dtype=torch.int64, device=self.device).contiguous()
@@ -78,14 +82,19 @@ class Problem:
         self.nshots = int(self.src.shape[0])
         if self.rec.shape[0] != self.nshots:
             raise ValueError("src and rec need the same number of shots")
+        auto = form == "auto"
         self.grid = native.tp_grid(int(ndim), int(nx), int(ny), int(nz), float(h), float(dt), int(nt), int(order),
-                                   float(vmax), native.TIME_FORMS[form], int(sponge), float(sponge_eta))
+                                   float(vmax), native.TIME_FORMS["compensated" if auto else form], int(sponge),
+                                   float(sponge_eta))
         self.geom = native.tp_geom(self.nshots, int(self.src.shape[1]), self.src.data_ptr(),
                                    int(self.rec.shape[1]), self.rec.data_ptr())
+        if auto and not native.tp_form_supported(self.grid, self.geom):
+            self.grid.form = native.TIME_FORMS["levels"]
+        self.form = {v: k for k, v in native.TIME_FORMS.items()}[self.grid.form]
         self._ws = {}
 
     @classmethod
-    def from_workload(cls, w, nt=None, vmax=None, device="cuda", form="levels"):
+    def from_workload(cls, w, nt=None, vmax=None, device="cuda", form="auto"):
         vm = float(max(w.vel_true.max(), w.vel0.max())) if vmax is None else vmax
         return cls(w.ndim, w.nx, w.ny, w.nz, w.h, w.dt, w.nt if nt is None else nt, w.order, w.src, w.rec,
                    vmax=vm, device=device, form=form, sponge=getattr(w, "sponge", 0),

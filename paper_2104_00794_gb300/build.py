@@ -20,7 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libtprobe.so")
-SOURCES = ["tp_api.cu", "tp_stencil.cu", "tp_sweep3d_tma.cu", "tp_gemm.cu", "tp_kernels.cu", "tp_noalloc.cu", "tp_qr.cu", "tp_image.cu"]
+SOURCES = ["tp_api.cu", "tp_stencil.cu", "tp_sweep3d_tma.cu", "tp_sweep2d_cluster.cu", "tp_gemm.cu", "tp_kernels.cu",
+           "tp_noalloc.cu", "tp_qr.cu", "tp_image.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,6 +1,7 @@
 // C ABI of libtprobe (include/tprobe.h): argument checks, workspace layout
 // and the host-side time loops that enqueue the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -88,6 +89,15 @@ void prof_after(int, cudaStream_t s) {
 
 void set_last_error(const char* msg) { g_err = msg; }
 
+namespace {
+std::atomic<long long> g_wait_limit{0};  // 0: the default
+}  // namespace
+
+long long wait_limit_cycles() {
+  const long long v = g_wait_limit.load(std::memory_order_relaxed);
+  return v > 0 ? v : DEFAULT_WAIT_CYCLES;
+}
+
 Layout make_layout(int ndim, int nx, int ny, int nz) {
   Layout L;
   L.ndim = ndim;
@@ -129,6 +139,9 @@ struct Plan {
   Layout L{};
   Weights W{};
   int nshots = 0, nsrc = 0, nrec = 0, nt = 0, r = 0, T = 0, S = 0, kind = 0, acc = 0, form = 0;
+  bool c2d = false;  // 2-D batch on the persistent cluster path (tp_sweep2d_cluster.cu)
+  int comp = 0;      // compensated (double-float) forward
+  size_t o_e = 0;    // comp: bf16 low parts of two levels per shot
   float scale = 1.f;
   size_t bytes = 0;
   size_t o_scal = 0, o_part = 0, o_c2 = 0, o_f = 0, o_P = 0, o_V = 0, o_Q = 0, o_d = 0, o_soff = 0, o_roff = 0,
@@ -158,7 +171,8 @@ tp_status check_grid(const tp_grid* g) {
   if ((long long)g->nx * g->ny * g->nz > (1LL << 40)) return fail(TP_ERR_ARG, "grid too large");
   if (g->nx > (1 << 24) || g->nz > (1 << 24) || g->ny > (1 << 24)) return fail(TP_ERR_ARG, "grid extent too large");
   if (!(g->vmax >= 0.f)) return fail(TP_ERR_ARG, "vmax must be >= 0");
-  if (g->form != TP_FORM_LEVELS && g->form != TP_FORM_INCREMENT) return fail(TP_ERR_ARG, "unknown time form %d", g->form);
+  if (g->form != TP_FORM_LEVELS && g->form != TP_FORM_INCREMENT && g->form != TP_FORM_COMPENSATED)
+    return fail(TP_ERR_ARG, "unknown time form %d", g->form);
   if (g->sponge < 0 || !(g->sponge_eta >= 0.f) || !std::isfinite(g->sponge_eta))
     return fail(TP_ERR_ARG, "sponge width must be >= 0 and sponge_eta finite and >= 0");
   return TP_OK;
@@ -215,6 +229,12 @@ tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe
   P->o_cr = take(cur, (size_t)ns * P->nrec * sizeof(float));
   P->o_c2 = take(cur, fb);
   P->form = g->form;
+  P->comp = g->form == TP_FORM_COMPENSATED;
+  P->c2d = g->form != TP_FORM_INCREMENT && cluster2d_fits(P->L, P->W, P->nshots, P->nsrc, P->nrec, P->comp);
+  if (P->comp && !P->c2d)
+    return fail(TP_ERR_ARG, "the compensated form needs a 2-D grid without an absorbing layer whose shot fits one "
+                            "thread-block cluster, with at most 1024 sources and receivers per shot");
+  if (P->comp) P->o_e = take(cur, (size_t)2 * ns * P->L.field * 2);  // bf16 low parts, two levels per shot
   if (P->form == TP_FORM_INCREMENT) P->o_w = take(cur, (size_t)ns * fb);  // the increment field of each shot
   switch (op) {
     case TP_OP_FORWARD:
@@ -373,13 +393,58 @@ tp_status point(const Ctx& c, const float* samp, long long samp_ss, const long l
     if (s_ != TP_OK) return s_;       \
   } while (0)
 
+// Arguments of a persistent 2-D launch over family f (level l of a shot in
+// slot l mod f.fs: every family passed to the loops below stores level t at
+// level(t) = t mod f.fs).
+Cluster2dArgs cluster_args(const Ctx& c, const Fam& f, int dir, int lev0, int nsteps, bool fresh, int comp) {
+  const Plan& P = c.P;
+  Cluster2dArgs a{};
+  a.L = P.L;
+  a.W = P.W;
+  a.nshots = P.nshots;
+  a.comp = comp;
+  a.dir = dir;
+  a.lev0 = lev0;
+  a.nsteps = nsteps;
+  a.fresh = fresh ? 1 : 0;
+  a.ring = c.at<float>(f.off);
+  a.nslots = f.fs;
+  a.ring_ss = c.ss(f);
+  a.eslots = comp ? c.at<char>(P.o_e) : nullptr;
+  a.e_ss = 2 * P.L.field;
+  a.c2 = c.at<float>(P.o_c2);
+  return a;
+}
+
 // Forward loop (Algorithm 1 lines 0-3).  Level t of every shot lives in
 // field level(t) of family f.  d (may be null) receives R u[t];
-// after_level(t) runs once level t is complete (sources injected).
-template <class LevelFn, class AfterFn>
-tp_status forward_loop(const Ctx& c, const Fam& f, LevelFn level, const float* wav, float* d, AfterFn after_level) {
+// after_level(t) runs once level t is complete (sources injected).  On the
+// 2-D cluster path the steps between two levels that closes() marks (the
+// levels after which after_level launches work) run as one persistent launch
+// that samples and injects by itself.
+template <class LevelFn, class AfterFn, class ClosesFn>
+tp_status forward_loop(const Ctx& c, const Fam& f, LevelFn level, const float* wav, float* d, AfterFn after_level,
+                       ClosesFn closes) {
   const Plan& P = c.P;
   const long long dss = (long long)P.nt * P.nrec, wss = (long long)P.nt * P.nsrc, ss = c.ss(f);
+  if (P.c2d) {
+    if (P.comp) TRY(cudaMemsetAsync(c.at<char>(P.o_e), 0, (size_t)2 * P.nshots * P.L.field * 2, c.st));
+    for (int t = 1; t <= P.nt - 2;) {
+      int te = t;
+      while (te < P.nt - 2 && !closes(te + 1)) ++te;
+      Cluster2dArgs a = cluster_args(c, f, +1, t, te - t + 1, t == 1, P.comp);
+      a.inj_off = c.at<long long>(P.o_soff); a.inj_coef = c.at<float>(P.o_cs); a.ninj = P.nsrc;
+      a.inj_val = wav; a.inj_val_ss = wss; a.inj_shift = -1;  // q[t] enters level t + 1
+      if (d) {
+        a.samp_off = c.at<long long>(P.o_roff); a.nsamp = P.nrec;
+        a.samp_out = d; a.samp_out_ss = dss; a.samp_shift = 0;
+      }
+      TRY(launch_cluster2d(a, c.st));
+      for (int lev = t + 1; lev <= te + 1; ++lev) TRYS(after_level(lev));
+      t = te + 1;
+    }
+    return TP_OK;
+  }
   if (P.form == TP_FORM_INCREMENT)  // u[1] - u[0] = 0
     TRY(cudaMemsetAsync(c.at<char>(P.o_w), 0, (size_t)P.nshots * P.L.field * sizeof(float), c.st));
   for (int t = 1; t <= P.nt - 2; ++t) {
@@ -397,13 +462,31 @@ tp_status forward_loop(const Ctx& c, const Fam& f, LevelFn level, const float* w
 
 // Adjoint loop (Algorithm 1 lines 4-7) driven by s[nshots][nt][nrec].
 // q_out (may be null) receives S lambda[t+1] at row t; acc/aval accumulate
-// sum_k lambda[k][src] q[k-1] for the full gradient's source term.
-template <class LevelFn, class AfterFn>
+// sum_k lambda[k][src] q[k-1] for the full gradient's source term.  Without
+// acc, a 2-D batch runs on the cluster path as in forward_loop (levels form).
+template <class LevelFn, class AfterFn, class ClosesFn>
 tp_status adjoint_loop(const Ctx& c, const Fam& f, LevelFn level, const float* s, float* q_out, double* acc,
-                       const float* aval, AfterFn after_level) {
+                       const float* aval, AfterFn after_level, ClosesFn closes) {
   const Plan& P = c.P;
   const long long sss = (long long)P.nt * P.nrec, qss = (long long)P.nt * P.nsrc, ss = c.ss(f);
   const bool samp = q_out || acc;
+  if (P.c2d && !acc) {
+    for (int j = P.nt - 1; j >= 2;) {
+      int je = j;
+      while (je > 2 && !closes(je)) --je;
+      Cluster2dArgs a = cluster_args(c, f, -1, j + 1, j - je + 1, j == P.nt - 1, 0);
+      a.inj_off = c.at<long long>(P.o_roff); a.inj_coef = c.at<float>(P.o_cr); a.ninj = P.nrec;
+      a.inj_val = s; a.inj_val_ss = sss; a.inj_shift = 0;  // s[j] enters lambda[j]
+      if (q_out) {
+        a.samp_off = c.at<long long>(P.o_soff); a.nsamp = P.nsrc;
+        a.samp_out = q_out; a.samp_out_ss = qss; a.samp_shift = -1;  // (F^T s)[j - 1] = S lambda[j]
+      }
+      TRY(launch_cluster2d(a, c.st));
+      for (int lev = j; lev >= je; --lev) TRYS(after_level(lev));
+      j = je - 1;
+    }
+    return TP_OK;
+  }
   if (P.form == TP_FORM_INCREMENT)  // lambda[nt] - lambda[nt+1] = 0
     TRY(cudaMemsetAsync(c.at<char>(P.o_w), 0, (size_t)P.nshots * P.L.field * sizeof(float), c.st));
   for (int j = P.nt - 1; j >= 2; --j) {
@@ -444,6 +527,21 @@ using namespace tp;
 
 extern "C" {
 
+tp_status tp_form_supported(const tp_grid* grid, const tp_geom* geom) {
+  TRYS(check_grid(grid));
+  if (!geom) return fail(TP_ERR_ARG, "geom is NULL");
+  if (geom->nshots < 1 || geom->nsrc < 1 || geom->nrec < 1) return fail(TP_ERR_ARG, "nshots, nsrc, nrec must be >= 1");
+  if (grid->form == TP_FORM_COMPENSATED) {
+    const Layout L = make_layout(grid->ndim, grid->nx, grid->ny, grid->nz);
+    Weights W = stencil_weights(grid->order);
+    W.sw = grid->sponge_eta > 0.f ? grid->sponge : 0;
+    if (!cluster2d_fits(L, W, geom->nshots, geom->nsrc, geom->nrec, true))
+      return fail(TP_ERR_ARG, "the compensated form needs a 2-D grid without an absorbing layer whose shot fits one "
+                              "thread-block cluster, with at most 1024 sources and receivers per shot");
+  }
+  return TP_OK;
+}
+
 size_t tp_workspace_bytes(int op, const tp_grid* grid, const tp_geom* geom, const tp_probe* probe) {
   Plan P;
   if (make_plan(op, grid, geom, probe, &P) != TP_OK) return 0;
@@ -462,7 +560,7 @@ tp_status tp_forward(const tp_grid* grid, const tp_geom* geom, const float* vel,
   TRY(cudaMemsetAsync(d_out, 0, (size_t)P.nshots * P.nt * P.nrec * sizeof(float), c.st));
   const Fam f{P.o_f, (int)P.nf, 3};
   auto level = [](int t) { return t % 3; };
-  TRYS(forward_loop(c, f, level, wavelet, d_out, [](int) { return TP_OK; }));
+  TRYS(forward_loop(c, f, level, wavelet, d_out, [](int) { return TP_OK; }, [](int) { return false; }));
   return TP_OK;
 }
 
@@ -478,7 +576,7 @@ tp_status tp_adjoint(const tp_grid* grid, const tp_geom* geom, const float* vel,
   TRY(cudaMemsetAsync(q_out, 0, (size_t)P.nshots * P.nt * P.nsrc * sizeof(float), c.st));
   const Fam f{P.o_f, (int)P.nf, 3};
   auto level = [](int t) { return t % 3; };
-  TRYS(adjoint_loop(c, f, level, d_in, q_out, nullptr, nullptr, [](int) { return TP_OK; }));
+  TRYS(adjoint_loop(c, f, level, d_in, q_out, nullptr, nullptr, [](int) { return TP_OK; }, [](int) { return false; }));
   return TP_OK;
 }
 
@@ -486,6 +584,15 @@ tp_status tp_adjoint(const tp_grid* grid, const tp_geom* geom, const float* vel,
 
 namespace tp {
 namespace {
+
+// adjoint windows: levels top .. bottom with top = nt - 1 - k T, bottom =
+// max(2, top - T + 1); a window closes at its bottom level
+auto adj_window_closes(int nt, int T) {
+  return [=](int lev) {
+    const int top = nt - 1 - ((nt - 1 - lev) / T) * T;
+    return lev == std::max(2, top - T + 1);
+  };
+}
 
 GemmArgs gemm_args(const Ctx& c, float* Q) {
   const Plan& P = c.P;
@@ -518,17 +625,22 @@ tp_status probed_forward_impl(const Ctx& c, const tp_probe* probe, const float* 
   g.P = Pacc;
   g.qshift = 1;
   const int jlast = nt - 2;
-  auto fwd_after = [&](int lev) -> tp_status {
-    if (lev < 2 || lev > jlast) return TP_OK;
+  // a window of levels w0 .. w0 + T - 1 (from level 2; the last one ends at nt - 2) closes at its last level
+  auto closes = [=](int lev) {
+    if (lev < 2 || lev > jlast) return false;
     const int w0 = 2 + ((lev - 2) / T) * T;
-    if (lev == std::min(w0 + T - 1, jlast)) {
+    return lev == std::min(w0 + T - 1, jlast);
+  };
+  auto fwd_after = [&](int lev) -> tp_status {
+    if (closes(lev)) {
+      const int w0 = 2 + ((lev - 2) / T) * T;
       g.level0 = w0;
       g.nlev = lev - w0 + 1;
       TRY(launch_probe_gemm(g, c.st));
     }
     return TP_OK;
   };
-  return forward_loop(c, ring, level, wavelet, d, fwd_after);
+  return forward_loop(c, ring, level, wavelet, d, fwd_after, closes);
 }
 
 // Single-accumulator form (TP_ACC_F32_FOLD): ubar_i = c2 S(P_i) + dt^2 v^2 S^T qbar_i
@@ -577,7 +689,7 @@ tp_status probed_backward_fold(const Ctx& c, const tp_grid* grid, const tp_geom*
     }
     return TP_OK;
   };
-  TRYS(adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after));
+  TRYS(adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after, adj_window_closes(nt, T)));
   TRY(launch_finish_grad(P.L, vel, tmp, P.nshots, P.L.field, P.scale / (grid->dt * grid->dt), grad, c.st, 0));
   if (wrt_velocity) TRY(launch_chain_velocity(vel, grad, (long long)P.L.nx * P.L.ny * P.L.nz, c.st));
   TRYS(grad_norm(c, grad, gnorm));
@@ -608,7 +720,7 @@ tp_status adjoint_probes(const Ctx& c, const float* s, const float* Q) {
     }
     return TP_OK;
   };
-  return adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after);
+  return adjoint_loop(c, ring, level, s, nullptr, nullptr, nullptr, adj_after, adj_window_closes(nt, T));
 }
 
 // Algorithm 1 lines 4-8: adjoint sweep driven by s (all shots), vbar_i =
@@ -787,7 +899,7 @@ tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float
   TRY(cudaMemsetAsync(d, 0, (size_t)P.nshots * nt * P.nrec * sizeof(float), c.st));
   const Fam fh{P.o_f, (int)P.nf, nt}, fl{P.o_P, 3 * P.nshots, 3}, fG{P.o_gacc, P.nshots, 1};
   auto hist = [](int t) { return t; };
-  TRYS(forward_loop(c, fh, hist, wavelet, d, [](int) { return TP_OK; }));
+  TRYS(forward_loop(c, fh, hist, wavelet, d, [](int) { return TP_OK; }, [](int) { return false; }));
   TRYS(misfit_and_residual(c, d, d_obs, misfit));
   // adjoint with the imaging condition of Eq. 3 in its stencil form:
   // gacc_s += lambda_s[j] * S(u_s[j-1])   (udd[j] = v^2 (L u[j-1] + S^T q[j-1]))
@@ -797,7 +909,7 @@ tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float
     TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
     return TP_OK;
   };
-  TRYS(adjoint_loop(c, fl, lam, d, nullptr, c.at<double>(P.o_sacc), wavelet, imaging));
+  TRYS(adjoint_loop(c, fl, lam, d, nullptr, c.at<double>(P.o_sacc), wavelet, imaging, [](int) { return true; }));
   TRY(launch_finish_grad(P.L, vel, c.at<float>(P.o_gacc), P.nshots, P.L.field, 1.0f / (grid->h * grid->h), grad,
                          c.st));
   TRY(launch_source_term(P.L, vel, geom->src, c.at<long long>(P.o_soff), P.nsrc, P.nshots, 1.0f, nullptr, nullptr, 0,
@@ -829,6 +941,12 @@ tp_status tp_workspace_status(void* ws, size_t ws_bytes, void* stream) {
 }
 
 const char* tp_last_error(void) { return g_err.c_str(); }
+
+tp_status tp_set_wait_limit(int64_t cycles) {
+  if (cycles < 0) return fail(TP_ERR_ARG, "the wait limit must be >= 0 (got %lld)", (long long)cycles);
+  g_wait_limit.store(cycles, std::memory_order_relaxed);
+  return TP_OK;
+}
 
 tp_status tp_profile_begin(int max_launches) {
   std::lock_guard<std::mutex> lk(g_prof.m);

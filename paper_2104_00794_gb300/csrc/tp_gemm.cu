@@ -26,8 +26,6 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
-#include <cstdlib>
-#include <cstring>
 
 #include "tp_internal.h"
 
@@ -775,21 +773,15 @@ int gemm_kpad(int T) { return T <= 32 ? 32 : (T <= 64 ? 64 : 128); }
 cudaError_t launch_probe_gemm(const GemmArgs& a, cudaStream_t s) {
   if (a.nlev <= 0) return cudaSuccess;
   prof_before(2, s);  // TP_KERNEL_PROBE_GEMM
-  static const int variant = [] {  // TP_PROBE_GEMM=regs selects the register-staged kernel
-    const char* e = getenv("TP_PROBE_GEMM");
-    return (e && strcmp(e, "regs") == 0) ? 1 : 0;
-  }();
   cudaError_t e;
-  if (a.acc != 0 || (a.r <= GRP && variant == 0)) {  // bf16 storage and dot mode exist on this path only (r <= 32)
+  if (a.acc != 0 || a.r <= GRP) {  // bf16 storage and dot mode exist on this path only (r <= 32)
 #define TP_WS(KPV) (a.acc == 0 ? launch_ws<KPV, 0>(a, s)                                    \
                            : (a.acc == 1 ? launch_ws<KPV, 1>(a, s)                         \
                                          : (a.acc == 2 ? launch_ws<KPV, 2>(a, s) : launch_ws<KPV, 3>(a, s))))
     e = a.nlev <= 32 ? TP_WS(32) : (a.nlev <= 64 ? TP_WS(64) : TP_WS(128));
 #undef TP_WS
-  } else if (a.nlev <= 32) {
-    e = a.r <= 16 ? launch_kp<32, 16>(a, s) : (a.r <= 32 ? launch_kp<32, 32>(a, s) : launch_kp<32, 0>(a, s));
-  } else {
-    e = a.r <= 16 ? launch_kp<64, 16>(a, s) : (a.r <= 32 ? launch_kp<64, 32>(a, s) : launch_kp<64, 0>(a, s));
+  } else {  // r > 32 (e.g. identity probes): the register-staged kernel, T <= 64
+    e = a.nlev <= 32 ? launch_kp<32, 0>(a, s) : launch_kp<64, 0>(a, s);
   }
   prof_after(2, s);
   return e;

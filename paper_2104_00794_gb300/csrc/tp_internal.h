@@ -111,6 +111,35 @@ cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const St
 bool encode_field_map(const Layout& L, const void* base, long long nfields, int esize, int box_x, int box_y,
                       int box_fields, CUtensorMap* out);
 
+// ---------------------------------------------------------------- 2-D cluster stepping
+// Persistent 2-D time stepping (tp_sweep2d_cluster.cu): one thread-block
+// cluster per shot holds the shot's levels in shared memory and runs nsteps
+// steps per launch, with in-kernel injection (entries at one node summed in
+// index order) and sampling.  Forward (dir = +1): step i forms level
+// lev0 + i + 1 from lev0 + i and lev0 + i - 1; adjoint (dir = -1): level
+// lev0 - i - 1 from lev0 - i and lev0 - i + 1.  Every new level is written to
+// ring slot (level mod nslots) of its shot; the launch starts from the ring
+// slots of lev0 and lev0 - dir (zero when fresh).  comp: double-float levels
+// (low parts in bf16 slots eslots + shot * e_ss + (level mod 2) * field,
+// written for the last two levels of a launch).  Injection: new level at
+// inj_off[s][k] += inj_coef[s][k] * inj_val[s][new level + inj_shift][k];
+// sampling: samp_out[s][new level + samp_shift][j] = new level at samp_off[s][j].
+struct Cluster2dArgs {
+  Layout L;
+  Weights W;
+  int nshots, comp, dir, lev0, nsteps, fresh;
+  float* ring; int nslots; long long ring_ss;
+  void* eslots; long long e_ss;
+  const float* c2;
+  const long long* inj_off; const float* inj_coef; int ninj;
+  const float* inj_val; long long inj_val_ss; int inj_shift;
+  const long long* samp_off; int nsamp; float* samp_out; long long samp_out_ss; int samp_shift;
+};
+cudaError_t launch_cluster2d(const Cluster2dArgs& a, cudaStream_t s);
+// whether the cluster path can run a batch of this grid (2-D, no absorbing
+// layer, a shot's bands fit one cluster, at most 1024 sources and receivers)
+bool cluster2d_fits(const Layout& L, const Weights& W, int nshots, int nsrc, int nrec, bool comp);
+
 // ---------------------------------------------------------------- probe GEMM
 // P[s][i][x] += sum_{k < nlev} ring[s][(level0 + k) mod nslots][x] * Q[s][level0 + k + qshift][i]
 // with Q rows outside [qlo, qhi] read as zero.  tcgen05 (kind::tf32) with a
@@ -201,16 +230,24 @@ cudaError_t launch_source_term(const Layout& L, const float* vel, const int64_t*
 // message returned by tp_last_error() on the calling thread
 void set_last_error(const char* msg);
 
+// Spin limit (SM clock cycles) of the bounded waits between the roles of the
+// pipelined kernels, read at launch: the value set by tp_set_wait_limit, else
+// DEFAULT_WAIT_CYCLES (about one second).  Waits that only drain a kernel's
+// own copies before it exits always use the default.
+constexpr long long DEFAULT_WAIT_CYCLES = 2000000000LL;
+long long wait_limit_cycles();
+
 // ---------------------------------------------------------------- profiling
 void prof_before(int kind, cudaStream_t s);
 void prof_after(int kind, cudaStream_t s);
 
-// Raises kernel K's dynamic shared-memory limit to `bytes` on the current
-// device, once per device: a function attribute belongs to the device's
+// Raises kernel K's dynamic shared-memory limit to `bytes` (and, if asked,
+// allows clusters above the portable size) on the current device, once per
+// device: a function attribute belongs to the device's
 // context, so a process that launches on several devices sets it on each.
 // Thread-safe; devices beyond the first 64 are set on every call.
 template <auto K>
-cudaError_t smem_limit_once(int bytes) {
+cudaError_t smem_limit_once(int bytes, bool nonportable_cluster = false) {
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -218,6 +255,8 @@ cudaError_t smem_limit_once(int bytes) {
   const unsigned long long bit = dev < 64 ? 1ULL << dev : 0ULL;
   if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
   e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && nonportable_cluster)
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }

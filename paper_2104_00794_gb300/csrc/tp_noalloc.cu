@@ -11,11 +11,13 @@
 //
 // The array lives in every GPU that loads the library, until the process
 // exits.  Host code must not pass the array's name to a kernel: in host code
-// it is only a stand-in for the symbol.  The device address is looked up once
-// per device with cudaGetSymbolAddress, with that device current, on the
-// first call made on that device.  Every call overwrites the partials it
-// uses before reading them, so nothing has to start at zero; calls that
-// overlap on the GPU (for example on two streams) race on the array.
+// it is only a stand-in for the symbol.  The device address comes from
+// cudaGetSymbolAddress with the calling device current: on every call made
+// outside stream capture, and from the last such call during capture (so the
+// first call on a device must come before any capture).  Every call
+// overwrites the partials it uses before reading them, so nothing has to
+// start at zero; calls that overlap on the GPU (for example on two streams)
+// race on the array.
 #include <cstdio>
 #include <mutex>
 
@@ -67,18 +69,25 @@ __global__ void __launch_bounds__(NA_THREADS) na_finalize_kernel(const double* p
   if (threadIdx.x == 0) *out = 0.5 * t;
 }
 
-// device address of g_noalloc_partials, looked up once per device
+// device address of g_noalloc_partials on each device.  Outside stream capture
+// it is looked up again on every call (a cheap host call), so an address made
+// stale by a device reset is never used; during capture the address cached by
+// the last call outside capture on that device is used, because a lookup then
+// could load the module inside the capture.
 constexpr int NA_MAX_DEVICES = 64;
 double* g_na_ptr[NA_MAX_DEVICES] = {};
 std::mutex g_na_mutex;
 
-cudaError_t na_scratch(double** out) {
+cudaError_t na_scratch(cudaStream_t st, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_na_mutex);
-  if (!g_na_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone || !g_na_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);  // the current device is `dev`
     if (e != cudaSuccess) return e;
@@ -106,11 +115,11 @@ tp_status tp_misfit_noalloc(const float* d_syn, const float* d_obs, int64_t n, d
   if (n < 1) return na_fail(TP_ERR_ARG, "tp_misfit_noalloc: n must be >= 1");
   if (n > NA_CHUNK * NA_MAX_CHUNKS)
     return na_fail(TP_ERR_ARG, "tp_misfit_noalloc: n exceeds the fixed scratch (268435456 samples at most)");
-  double* scratch = nullptr;
-  cudaError_t e = na_scratch(&scratch);
-  if (e != cudaSuccess) return na_fail(TP_ERR_CUDA, "tp_misfit_noalloc: cudaGetSymbolAddress failed", e);
-  const int nchunks = (int)((n + NA_CHUNK - 1) / NA_CHUNK);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* scratch = nullptr;
+  cudaError_t e = na_scratch(st, &scratch);
+  if (e != cudaSuccess) return na_fail(TP_ERR_CUDA, "tp_misfit_noalloc: scratch lookup failed", e);
+  const int nchunks = (int)((n + NA_CHUNK - 1) / NA_CHUNK);
   prof_before(4, st);
   na_partial_kernel<<<nchunks, NA_THREADS, 0, st>>>(d_syn, d_obs, n, scratch);
   na_finalize_kernel<<<1, NA_THREADS, 0, st>>>(scratch, nchunks, misfit);

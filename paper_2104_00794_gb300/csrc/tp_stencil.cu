@@ -1,19 +1,18 @@
 // Leapfrog stencil sweeps (Algorithm 1 lines 1 and 5, operators f and f^T)
-// and the stencil-form imaging sweep, for 2-D and 3-D padded fields.
+// and the stencil-form imaging sweep for 2-D padded fields, and the dispatch
+// of every sweep (3-D ones run in tp_sweep3d_tma.cu).
 //
-// Design (HBM-bound, ~16 B per grid point per step):
-//   * every CTA owns an x-y tile (3-D) or an x strip (2-D) and sweeps a chunk
-//     of z planes; each thread owns 4 consecutive x points (float4 access);
-//   * the z neighbours of the thread's points live in a register queue of
-//     2R+1 float4 values, the current plane (with its x/y halo) in shared
+// Design (~16 B per grid point per step; a 2-D batch usually sits in L2):
+//   * every warp owns an x strip of 128 points and sweeps a chunk of z rows;
+//     each lane owns 4 consecutive x points (float4 access);
+//   * the z neighbours of the lane's points live in a register queue of
+//     2R+1 float4 values, the current row (with its x halo) in shared
 //     memory, so each haloed value is read from L2/HBM about once per sweep;
-//   * all global loads of plane z+1 (queue head, halo, older level,
-//     coefficient) are issued before plane z is computed;
+//   * all global loads of row z+1 (queue head, halo, older level,
+//     coefficient) are issued before row z is computed;
 //   * zero halo layers of the padded layout supply the Dirichlet boundary,
 //     so no load is predicated.
 #include <algorithm>
-#include <cstdlib>
-#include <cstring>
 
 #include "tp_internal.h"
 
@@ -63,103 +62,6 @@ __device__ __forceinline__ void store_masked(float* out, long long idx, float4 v
     if (x + 1 < nx) out[idx + 1] = v.y;
     if (x + 2 < nx) out[idx + 2] = v.z;
     if (x + 3 < nx) out[idx + 3] = v.w;
-  }
-}
-
-// ------------------------------------------------------------------ 3-D
-constexpr int T3X = 16;  // float4 columns per tile (64 points)
-constexpr int T3Y = 16;  // rows per tile
-
-template <int R, int MODE, bool DAMP>
-__global__ void __launch_bounds__(T3X * T3Y, 2)
-sweep3d(Layout L, Weights W, PlainArgs a, int bz, int nzc) {
-  __shared__ float4 sm[T3Y + 2 * R][T3X + 2];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int shot = blockIdx.z / nzc, zc = blockIdx.z % nzc;
-  const int x0 = blockIdx.x * (4 * T3X), y0 = blockIdx.y * T3Y;
-  const int x = x0 + 4 * tx, y = y0 + ty;
-  const int zb = zc * bz, ze = min(L.nz, zb + bz);
-  if (zb >= ze) return;
-
-  const float* src = a.src + shot * a.src_ss;
-  const float* p1 = a.p1 + shot * a.p1_ss;
-  const float* p2 = a.p2 + shot * a.p2_ss;
-  float* out = a.out + shot * a.out_ss;
-  const long long pl = L.plane;
-  // offset of (z = 0, row, column) for this thread's own points and halos
-  const long long colc = (long long)(y + H) * L.px + (x + HX) + (long long)H * pl;
-  const long long coly0 = (long long)(y0 - R + ty + H) * L.px + (x + HX) + (long long)H * pl;
-  const long long coly1 = (long long)(y0 + T3Y + ty + H) * L.px + (x + HX) + (long long)H * pl;
-  const long long colxl = (long long)(y + H) * L.px + (x0 - 4 + HX) + (long long)H * pl;
-  const long long colxr = (long long)(y + H) * L.px + (x0 + 4 * T3X + HX) + (long long)H * pl;
-  const bool hy = ty < R, hxl = tx == 0, hxr = tx == T3X - 1;
-
-  float4 q[2 * R + 1];
-#pragma unroll
-  for (int k = 0; k < 2 * R; ++k) q[k] = ld4(src, colc + (long long)(zb - R + k) * pl);
-  float4 nq = ld4(src, colc + (long long)(zb + R) * pl);
-  float4 n1 = ld4(p1, colc + (long long)zb * pl);
-  float4 n2 = ld4(p2, colc + (long long)zb * pl);
-  float4 nh0 = make_float4(0.f, 0.f, 0.f, 0.f), nh1 = nh0, nhx = nh0;
-  if (hy) {
-    nh0 = ld4(src, coly0 + (long long)zb * pl);
-    nh1 = ld4(src, coly1 + (long long)zb * pl);
-  }
-  if (hxl) nhx = ld4(src, colxl + (long long)zb * pl);
-  if (hxr) nhx = ld4(src, colxr + (long long)zb * pl);
-
-  for (int z = zb; z < ze; ++z) {
-    q[2 * R] = nq;
-    // stage plane z (centre from the queue, halo from the prefetch registers)
-    sm[ty + R][tx + 1] = q[R];
-    if (hy) {
-      sm[ty][tx + 1] = nh0;
-      sm[ty + T3Y + R][tx + 1] = nh1;
-    }
-    if (hxl) sm[ty + R][0] = nhx;
-    if (hxr) sm[ty + R][T3X + 1] = nhx;
-    const float4 c1 = n1, c2 = n2;
-    if (z + 1 < ze) {  // prefetch plane z+1 while plane z is computed
-      const long long zo = (long long)(z + 1) * pl;
-      nq = ld4(src, colc + zo + (long long)R * pl);
-      n1 = ld4(p1, colc + zo);
-      n2 = ld4(p2, colc + zo);
-      if (hy) {
-        nh0 = ld4(src, coly0 + zo);
-        nh1 = ld4(src, coly1 + zo);
-      }
-      if (hxl) nhx = ld4(src, colxl + zo);
-      if (hxr) nhx = ld4(src, colxr + zo);
-    }
-    __syncthreads();
-
-    const float4 xl = sm[ty + R][tx], xc = sm[ty + R][tx + 1], xr = sm[ty + R][tx + 2];
-    const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-    float s[4] = {0.f, 0.f, 0.f, 0.f};  // centred form (see tp_sweep3d_tma.cu)
-#pragma unroll
-    for (int k = 1; k <= R; ++k) {
-      const float4 yp = sm[ty + R + k][tx + 1], ym = sm[ty + R - k][tx + 1];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const float nb = ((v[4 + p + k] + v[4 + p - k]) + (comp(yp, p) + comp(ym, p))) +
-                         (comp(q[R + k], p) + comp(q[R - k], p));
-        s[p] = fmaf(W.w[k], fmaf(-6.0f, v[4 + p], nb), s[p]);
-      }
-    }
-    float res[4], inc[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float ad = (DAMP && MODE != MODE_IMAGE) ? sponge_a(L, W, z, y, x + p) : 0.f;
-      res[p] = epilogue<MODE>(v[4 + p], s[p], comp(c1, p), comp(c2, p), &inc[p], ad);
-    }
-    if (y < L.ny && x < L.nx) {
-      store_masked(out, colc + (long long)z * pl, make_float4(res[0], res[1], res[2], res[3]), x, L.nx);
-      if (MODE == MODE_INC)
-        store_masked(a.out2 + shot * a.out2_ss, colc + (long long)z * pl, make_float4(inc[0], inc[1], inc[2], inc[3]), x, L.nx);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
   }
 }
 
@@ -269,26 +171,6 @@ int num_sms() {
 }
 
 template <int R, int MODE>
-cudaError_t launch3d(const Layout& L, const Weights& W, const PlainArgs& a, cudaStream_t s) {
-  static const int occ = [] {  // the same on every device of this architecture
-    int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, sweep3d<R, MODE, false>, T3X * T3Y, 0);
-    return o > 0 ? o : 1;
-  }();
-  const int gx = (L.nx + 4 * T3X - 1) / (4 * T3X), gy = (L.ny + T3Y - 1) / T3Y;
-  const long long tiles = (long long)gx * gy * a.nshots;
-  const long long target = 2LL * occ * num_sms();
-  int nzc = (int)std::max<long long>(1, (target + tiles - 1) / tiles);
-  nzc = std::min(nzc, std::max(1, L.nz / 8));
-  const int bz = (L.nz + nzc - 1) / nzc;
-  nzc = (L.nz + bz - 1) / bz;
-  dim3 grid(gx, gy, nzc * a.nshots), block(T3X, T3Y);
-  if (MODE != MODE_IMAGE && W.sw > 0) sweep3d<R, MODE, true><<<grid, block, 0, s>>>(L, W, a, bz, nzc);
-  else sweep3d<R, MODE, false><<<grid, block, 0, s>>>(L, W, a, bz, nzc);
-  return cudaGetLastError();
-}
-
-template <int R, int MODE>
 cudaError_t launch2d(const Layout& L, const Weights& W, const PlainArgs& a, cudaStream_t s) {
   const int nxt = (L.nx + 127) / 128;
   const long long strips = (long long)nxt * a.nshots;
@@ -309,18 +191,14 @@ cudaError_t launch2d(const Layout& L, const Weights& W, const PlainArgs& a, cuda
 cudaError_t launch_sweep3d_tma(int mode, const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s,
                                int* err);
 
-// 3-D sweeps use the TMA-pipelined kernel (tp_sweep3d_tma.cu); the register
-// queue kernel above stays selectable with TP_SWEEP3D=plain for comparisons.
+// 3-D sweeps use the TMA-pipelined kernel (tp_sweep3d_tma.cu), 2-D ones the
+// warp-strip kernel above.
 cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& sa,
                            cudaStream_t s, int* err) {
   const int kind = mode == MODE_IMAGE ? 1 : 0;  // TP_KERNEL_IMAGING / TP_KERNEL_STENCIL
-  static const bool plain3d = [] {
-    const char* e = getenv("TP_SWEEP3D");
-    return e && strcmp(e, "plain") == 0;
-  }();
   prof_before(kind, s);
   cudaError_t e;
-  if (L.ndim == 3 && !plain3d) {
+  if (L.ndim == 3) {
     e = launch_sweep3d_tma(mode, L, W, sa, s, err);
   } else {
     PlainArgs a{sa.src.ptr(L, 0), (long long)sa.src.fs * L.field, sa.p1.ptr(L, 0), (long long)sa.p1.fs * L.field,
@@ -328,8 +206,7 @@ cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const St
 #define TP_DISPATCH(FN, RR)                                                   \
   (mode == MODE_STEP ? FN<RR, MODE_STEP>(L, W, a, s)                          \
                      : (mode == MODE_INC ? FN<RR, MODE_INC>(L, W, a, s) : FN<RR, MODE_IMAGE>(L, W, a, s)))
-    if (L.ndim == 3) e = W.R == 4 ? TP_DISPATCH(launch3d, 4) : TP_DISPATCH(launch3d, 2);
-    else e = W.R == 4 ? TP_DISPATCH(launch2d, 4) : TP_DISPATCH(launch2d, 2);
+    e = W.R == 4 ? TP_DISPATCH(launch2d, 4) : TP_DISPATCH(launch2d, 2);
 #undef TP_DISPATCH
   }
   prof_after(kind, s);

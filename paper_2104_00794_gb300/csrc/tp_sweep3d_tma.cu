@@ -25,8 +25,6 @@
 #include <cuda.h>
 
 #include <algorithm>
-#include <cstdlib>
-#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -38,7 +36,6 @@ namespace {
 
 constexpr int NCONS = 256;                 // consumer threads, 4 x points each
 constexpr int NTHREADS = NCONS + 32;       // + one producer warp
-constexpr long long SPIN_LIMIT = 2000000000LL;  // cycles (~1 s)
 
 // Tile BX x BY (BX/4 * BY == NCONS) and LA planes of lookahead.
 template <int R, int BX_, int BY_, int LA_>
@@ -65,6 +62,7 @@ struct TmaArgs {
   int nshots, ntx, nty;
   int nzc, zchunk;  // each tile column is cut into nzc chunks of zchunk planes
   long long items;  // tiles x shots x nzc work items
+  long long spin;   // limit of the role waits (cycles); the drain waits use DEFAULT_WAIT_CYCLES
   int* err;
 };
 
@@ -88,18 +86,38 @@ __device__ __forceinline__ bool bar_try(uint32_t b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; false on timeout or when another role has aborted
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, volatile int* abort_flag) {
-  if (bar_try(b, parity)) return true;
+// non-blocking probe of a phase (mbarrier.try_wait may suspend the thread in
+// hardware until the phase completes, longer than a short wait limit)
+__device__ __forceinline__ bool bar_test(uint32_t b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(b), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on timeout or when another role has aborted.  With the
+// default limit it polls with try_wait (the thread sleeps in hardware between
+// polls); with a shorter one, set through tp_set_wait_limit, with test_wait,
+// so that the limit is what ends the wait.
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, volatile int* abort_flag, long long limit) {
+  const bool quick = limit < DEFAULT_WAIT_CYCLES;
+  if (quick ? bar_test(b, parity) : bar_try(b, parity)) return true;
   const long long t0 = clock64();
-  while (!bar_try(b, parity)) {
+  while (!(quick ? bar_test(b, parity) : bar_try(b, parity))) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > SPIN_LIMIT) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
   }
   return true;
+}
+// the same for a consumer warp: one decision for the whole warp, so that no
+// lane leaves the plane loop while the others reach a warp-wide sync
+__device__ __forceinline__ bool warp_wait(uint32_t b, uint32_t parity, volatile int* abort_flag, long long limit) {
+  return __all_sync(0xffffffffu, bar_wait(b, parity, abort_flag, limit));
 }
 __device__ __forceinline__ void tma4(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                      uint32_t bar) {
@@ -179,7 +197,7 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
       const int fu = a.f_src + sg.shot * a.fs_src, f1 = a.f_p1 + sg.shot * a.fs_p1, f2 = a.f_p2 + sg.shot * a.fs_p2;
       for (int k = 0; k < nzs + 2 * R && ok; ++k) {
         const int su = ku % C::NSU;
-        if (ku >= (uint32_t)C::NSU && !bar_wait(emptyU + 8 * su, ((ku / C::NSU) - 1) & 1, abort_flag)) {
+        if (ku >= (uint32_t)C::NSU && !bar_wait(emptyU + 8 * su, ((ku / C::NSU) - 1) & 1, abort_flag, a.spin)) {
           ok = false;
           break;
         }
@@ -190,7 +208,7 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
         if (k >= 2 * R) {
           const int j = k - 2 * R;
           const int sp = kp % C::NSP;
-          if (kp >= (uint32_t)C::NSP && !bar_wait(emptyP + 8 * sp, ((kp / C::NSP) - 1) & 1, abort_flag)) {
+          if (kp >= (uint32_t)C::NSP && !bar_wait(emptyP + 8 * sp, ((kp / C::NSP) - 1) & 1, abort_flag, a.spin)) {
             ok = false;
             break;
           }
@@ -207,14 +225,14 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
       const uint32_t uses = ku > (uint32_t)s ? (ku - 1 - s) / C::NSU + 1 : 0;
       if (uses) {
         const long long t0 = clock64();
-        while (!bar_try(fullU + 8 * s, (uses - 1) & 1) && clock64() - t0 < SPIN_LIMIT) {}
+        while (!bar_try(fullU + 8 * s, (uses - 1) & 1) && clock64() - t0 < DEFAULT_WAIT_CYCLES) {}
       }
     }
     for (int s = 0; s < C::NSP; ++s) {
       const uint32_t uses = kp > (uint32_t)s ? (kp - 1 - s) / C::NSP + 1 : 0;
       if (uses) {
         const long long t0 = clock64();
-        while (!bar_try(fullP + 8 * s, (uses - 1) & 1) && clock64() - t0 < SPIN_LIMIT) {}
+        while (!bar_try(fullP + 8 * s, (uses - 1) & 1) && clock64() - t0 < DEFAULT_WAIT_CYCLES) {}
       }
     }
     return;
@@ -239,7 +257,7 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) {
       const uint32_t kk = ku + k, s = kk % C::NSU;
-      if (!bar_wait(fullU + 8 * s, (kk / C::NSU) & 1, abort_flag)) { ok = false; break; }
+      if (!warp_wait(fullU + 8 * s, (kk / C::NSU) & 1, abort_flag, a.spin)) { ok = false; break; }
       q[k] = U4[s * (C::UFL / 4) + cidx];
       if (k < R) {
         __syncwarp();
@@ -252,9 +270,9 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
     for (int j = 0; j < nzs && ok; ++j) {
       const uint32_t kc = ku + j + R, kn = ku + j + 2 * R, kq = kp + j;
       const uint32_t sc = kc % C::NSU, sn = kn % C::NSU, sp = kq % C::NSP;
-      if (!bar_wait(fullU + 8 * sn, (kn / C::NSU) & 1, abort_flag)) { ok = false; break; }
+      if (!warp_wait(fullU + 8 * sn, (kn / C::NSU) & 1, abort_flag, a.spin)) { ok = false; break; }
       q[2 * R] = U4[sn * (C::UFL / 4) + cidx];
-      if (!bar_wait(fullP + 8 * sp, (kq / C::NSP) & 1, abort_flag)) { ok = false; break; }
+      if (!warp_wait(fullP + 8 * sp, (kq / C::NSP) & 1, abort_flag, a.spin)) { ok = false; break; }
       const float4* Uc = U4 + sc * (C::UFL / 4);
       const float4 xl = Uc[cidx - 1], xc = Uc[cidx], xr = Uc[cidx + 1];
       const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
@@ -440,6 +458,7 @@ cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cu
   t.ntx = (L.nx + BX - 1) / BX;
   t.nty = (L.ny + BY - 1) / BY;
   t.err = err;
+  t.spin = wait_limit_cycles();
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

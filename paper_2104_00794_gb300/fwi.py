@@ -100,7 +100,12 @@ def invert(problem, vel0, wavelet, d_obs, vmin: float, vmax: float, iters: int, 
     `full=True` uses the full-storage gradient instead.  `mask` (the model's
     shape, 0/1) restricts the update; `step0` sets the first step (the largest
     entry of m moves by that fraction).  Returns the velocity model in ``x``
-    (device tensor, the shape of vel0)."""
+    (device tensor, the shape of vel0).
+
+    The line search's misfits go through tp_misfit_noalloc, whose scratch is
+    one array per device shared by every call in the process: two inversions
+    run at the same time in one process (threads on different streams) must
+    be serialised, or their misfits race on that array."""
     import torch
 
     dev = problem.device

@@ -22,7 +22,7 @@ PROBE_KINDS = {"rademacher": 0, "gaussian": 1, "identity": 2, "user": 3}
 OP_FORWARD, OP_ADJOINT, OP_GRADIENT_PROBED, OP_GRADIENT_FULL, OP_PROBED_FORWARD, OP_PROBED_BACKWARD = range(6)
 ACC_TYPES = {"f32": 0, "bf16": 1, "bf16_kahan": 2, "f32_fold": 3}
 IMAGE_CONDS = {"correlation": 0, "gradient": 1}
-TIME_FORMS = {"levels": 0, "increment": 1}
+TIME_FORMS = {"levels": 0, "increment": 1, "compensated": 2}
 KERNEL_KINDS = 6
 
 
@@ -86,11 +86,14 @@ def lib():
         L.tp_last_error.restype = ctypes.c_char_p
         L.tp_profile_begin.argtypes = [i32]
         L.tp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        L.tp_set_wait_limit.argtypes = [ctypes.c_int64]
+        L.tp_form_supported.argtypes = [G, E]
         L.tp_kernel_name.argtypes = [i32]
         L.tp_kernel_name.restype = ctypes.c_char_p
         for f in ("tp_forward", "tp_adjoint", "tp_gradient_probed", "tp_gradient_full", "tp_probes",
                   "tp_workspace_status", "tp_profile_begin", "tp_profile_end", "tp_misfit_noalloc",
-                  "tp_probed_forward", "tp_probed_backward", "tp_qr_probes", "tp_probed_image", "tp_residual"):
+                  "tp_probed_forward", "tp_probed_backward", "tp_qr_probes", "tp_probed_image", "tp_residual",
+                  "tp_set_wait_limit", "tp_form_supported"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
         return L
@@ -190,6 +193,18 @@ def tp_misfit_noalloc(d_syn, d_obs, n, misfit, stream):
 
 def tp_workspace_status(ws, ws_bytes, stream):
     _check(lib().tp_workspace_status(ws, ws_bytes, stream))
+
+
+def tp_form_supported(grid, geom) -> bool:
+    """Whether the library can run `grid` (its time form in particular) for
+    batches with geom's counts (no device work)."""
+    return lib().tp_form_supported(ctypes.byref(grid), ctypes.byref(geom)) == TP_OK
+
+
+def tp_set_wait_limit(cycles: int):
+    """Spin limit (SM cycles) of the pipelined kernels' role waits for the
+    launches that follow; 0 restores the default (about one second)."""
+    _check(lib().tp_set_wait_limit(int(cycles)))
 
 
 def tp_profile_begin(max_launches: int = 0):

@@ -166,3 +166,38 @@ def test_no_cpu_fallback_in_product_path():
                     src = fh.read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", src, re.M), f
                 assert "tp_oracle" not in src, f
+
+
+def test_form_supported_and_compensated_workspace(L):
+    """The compensated form runs 2-D grids whose shot fits one thread-block
+    cluster and no absorbing layer; elsewhere tp_form_supported (and every
+    sizing call) rejects it, and the levels form stays available."""
+    comp = native.TIME_FORMS["compensated"]
+    w4 = wl.config4()
+    g4 = _grid(w4)
+    g4.form = comp
+    assert native.tp_form_supported(g4, _geom(w4))
+    ws_comp = native.tp_workspace_bytes(native.OP_FORWARD, g4, _geom(w4))
+    g4.form = native.TIME_FORMS["levels"]
+    ws_lev = native.tp_workspace_bytes(native.OP_FORWARD, g4, _geom(w4))
+    assert ws_comp > ws_lev  # two bf16 low-part levels per shot
+    w3 = wl.config3(n=64, nt=10)
+    g3 = _grid(w3)
+    g3.form = comp
+    assert not native.tp_form_supported(g3, _geom(w3))
+    assert "2-D" in native.last_error()
+    assert L.tp_workspace_bytes(native.OP_FORWARD, ctypes.byref(g3), ctypes.byref(_geom(w3)), None) == 0
+    g4.form = comp
+    g4.sponge, g4.sponge_eta = 10, 50.0
+    assert not native.tp_form_supported(g4, _geom(w4))
+    big = native.tp_grid(2, 4000, 1, 3000, 10.0, 1e-3, 100, 8, 0.0, comp)
+    assert not native.tp_form_supported(big, native.tp_geom(1, 1, 0x1000, 10, 0x1000))
+    many = native.tp_geom(1, 1, 0x1000, 1025, 0x1000)  # more receivers per shot than one list holds
+    assert native.tp_form_supported(_grid(w4), many)  # the levels form takes any count
+    g4.sponge, g4.sponge_eta = 0, 0.0
+    assert not native.tp_form_supported(g4, many)
+
+
+def test_wait_limit_validation(L):
+    assert L.tp_set_wait_limit(-5) == native.TP_ERR_ARG
+    assert L.tp_set_wait_limit(0) == native.TP_OK

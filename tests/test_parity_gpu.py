@@ -9,6 +9,8 @@ Tolerances (stated by the hot-path contract, derived for fp32 arithmetic):
   * probes: bit-exact (integer hash, exactly representable values);
   * fp64 misfit: relative 1e-5 (inherits the fp32 trace error).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -261,28 +263,35 @@ def test_config1_exact_size():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("cfg,gtol", [("config2", GRAD_TOL), ("config4", 1.5e-4)])
-def test_config_2_4_shot_subset_full_nt(cfg, gtol):
+@pytest.mark.parametrize("cfg", ["config2", "config4"])
+def test_config_2_4_shot_subset_full_nt(cfg):
     """601 x 201 (order 8, r = 16 Gaussian, nt = 3000) and 801 x 301 (nt =
-    2500): two of the shots at the full time axis, in the batched launch.
+    2500): two of the shots at the full time axis, in the batched launch,
+    with the library's default form for these grids (the compensated
+    forward).  Traces and the probed gradient meet the contract's bounds.
 
-    Traces meet the 1e-5 bound after thousands of fp32 steps.  The gradient
-    bound follows from them: the adjoint source is the residual, whose
-    relative error is the trace error times |d| / |res|, and Eq. 4's sum over
-    probes cancels (the estimate is smaller than its terms), which multiplies
-    the relative error again.  Config 4's residual is 0.23 |d|, so with 1e-5
-    traces the probed gradient can sit at ~1.1e-4 (measured 1.07e-4; its
-    full-storage gradient 6e-5): its bound is 1.5e-4; config 2 (residual
-    0.53 |d|) keeps 1e-4."""
-    import dataclasses
+    Why the compensated forward: the probed gradient applies the Laplacian
+    to the probed forward field, which amplifies the grid-scale rounding
+    noise that fp32 levels collect over thousands of steps (config 4's
+    gradient sat at 1.07e-4 with the levels form although its traces were
+    within 7.5e-6); carrying the rounding of the levels as a bf16 low part
+    removes that noise."""
     w = getattr(wl, cfg)()
     k = [0, w.nshots - 1]
     w = dataclasses.replace(w, nshots=2, src=w.src[k], rec=w.rec[k], wavelet=np.ascontiguousarray(w.wavelet[k]))
-    p = problem(w)
+    p = api.Problem.from_workload(w)
+    assert p.form == "compensated"
     dobs = oracle_dobs(w)
     d = host(p.forward(to_dev(w.vel0), to_dev(w.wavelet)))
     assert rel_l2(d, oracle.batch_forward(w, w.vel0)) <= TRACE_TOL  # thousands of fp32 steps
     gp, sc = p.gradient_probed(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs),
                                api.ProbeSpec(kind="gaussian", r=16, T=32, seed=w.seed))
     ref, J = oracle.batch_gradient_probed(w, w.vel0, dobs)
-    assert rel_l2(host(gp), ref) <= gtol
+    err = rel_l2(host(gp), ref)
+    pl = api.Problem.from_workload(w, form="levels")
+    gl, _ = pl.gradient_probed(to_dev(w.vel0), to_dev(w.wavelet), to_dev(dobs),
+                               api.ProbeSpec(kind="gaussian", r=16, T=32, seed=w.seed))
+    err_levels = rel_l2(host(gl), ref)
+    print(f"{cfg}: probed gradient {err:.3e} (levels form {err_levels:.3e}) after {w.nt} steps")
+    assert err <= GRAD_TOL, err
+    assert err < err_levels

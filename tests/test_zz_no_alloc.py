@@ -6,13 +6,13 @@ latency-critical loop that must not allocate).  tp_misfit_noalloc serves
 them with scratch space that lives inside the library, so it takes no
 workspace.  Here it is called through the C ABI twice in a row and checked
 against the misfit that tp_gradient_full returns for the same model and data,
-within the misfit tolerance of the other parity tests.
+within the misfit tolerance of the other parity tests; then over a
+descending run of sizes (two chunks of the scratch, an exact chunk, one
+sample past it, a single sample) against the same sum taken on the host.
 
 This file is named to be collected last: if it fails, a run that stops at the
 first failure has already run every other test.
 """
-import ctypes
-
 import numpy as np
 import pytest
 import torch
@@ -42,6 +42,28 @@ def test_misfit_noalloc_matches_gradient_full_twice(cuda_lib):
     assert got[0] == pytest.approx(ref, rel=1e-5)
     assert got[1] == pytest.approx(ref, rel=1e-5)
     assert got[0] == got[1]
+
+
+def test_misfit_noalloc_sizes_descending(cuda_lib):
+    """Each call after a longer one: a result that leaned on partial sums left
+    in the shared array by the previous call would be off.  The host sum takes
+    the residual in fp32 (as the kernel does) and its squares in fp64, so only
+    the order of the fp64 additions differs."""
+    rng = np.random.default_rng(7)
+    n_max = 90_900
+    d = rng.standard_normal(n_max).astype(np.float32)
+    dobs = rng.standard_normal(n_max).astype(np.float32)
+    dd, do = to_dev(d), to_dev(dobs)
+    sizes = [90_900, 65_537, 65_536, 1]
+    out = torch.full((len(sizes),), -1.0, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for k, n in enumerate(sizes):
+        native.tp_misfit_noalloc(dd.data_ptr(), do.data_ptr(), n, out.data_ptr() + 8 * k, stream)
+    got = host(out)
+    for k, n in enumerate(sizes):
+        r = (d[:n] - dobs[:n]).astype(np.float64)
+        ref = 0.5 * float(np.sum(r * r))
+        assert got[k] == pytest.approx(ref, rel=1e-11), (n, got[k], ref)
 
 
 def test_misfit_noalloc_rejects_bad_sizes(cuda_lib):
