@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--cpu-nt", type=int, default=48, help="time levels of the bounded CPU sample")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (p50/p99) leg")
     ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--no-2d", action="store_true",
+                    help="skip the 2-D configurations (1, 2, 4) and config 4's precision leg (N = 1 only)")
     return ap.parse_args()
 
 
@@ -264,6 +266,92 @@ def run_serving(args, rank):
     return s
 
 
+def graph_time(fn, steps, warmup):
+    """ms per call of fn captured once as a CUDA graph and replayed (CUDA
+    events on the current stream, W warm-up replays)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        g = torch.cuda.CUDAGraph()
+        g.capture_begin()
+        fn()
+        g.capture_end()
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_2d(args):
+    """The 2-D configurations (L2-resident batches on the persistent cluster
+    path): probed-gradient Gpts/s in the default form and in the levels form,
+    and config 4's errors against FP64 on two of its shots (the default
+    compensated form, the levels form, bf16 and bf16 + compensation storage,
+    and the autograd backward)."""
+    import torch
+    import oracle
+    from paper_2104_00794_gb300 import api
+    from paper_2104_00794_gb300 import workloads as wl
+    from paper_2104_00794_gb300.autograd import modeling
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    out = {}
+    for name in ("config1", "config2", "config4"):
+        w = getattr(wl, name)()
+        vel_true, vel0, wav = dev(w.vel_true), dev(w.vel0), dev(w.wavelet)
+        rec = {"workload": w.name, "shots": w.nshots}
+        for form in ("auto", "levels"):
+            p = api.Problem.from_workload(w, form=form)
+            d_obs = p.forward(vel_true, wav).clone()
+            spec = api.ProbeSpec(kind=w.probe_kind, r=w.r, T=w.T, seed=w.seed)
+            grad = torch.empty(p.shape, dtype=torch.float32, device="cuda")
+            scal = torch.empty(2, dtype=torch.float64, device="cuda")
+            ms = graph_time(lambda: p.gradient_probed(vel0, wav, d_obs, spec, grad=grad, scalars=scal),
+                            args.steps, args.warmup)
+            key = "default" if form == "auto" else "levels"
+            rec[key] = {"form": p.form, "ms_per_step": ms, "value": 2.0 * w.N * w.nt * w.nshots / (ms * 1e-3) / 1e9,
+                        "unit": "Gpts/s"}
+            p.release()
+            del p
+        out[name] = rec
+    # config 4's precision on two of its shots (the oracle takes about a minute per pair)
+    w = wl.config4()
+    k = [0, w.nshots - 1]
+    w = dataclasses.replace(w, nshots=2, src=w.src[k], rec=w.rec[k], wavelet=np.ascontiguousarray(w.wavelet[k]))
+    dobs = oracle.batch_forward(w, w.vel_true).astype(np.float32)
+    t0 = time.perf_counter()
+    ref, J = oracle.batch_gradient_probed(w, w.vel0, dobs)
+    t_or = time.perf_counter() - t0
+    vel0, wav, d_obs = dev(w.vel0), dev(w.wavelet), dev(dobs)
+    rel = lambda g: float(np.linalg.norm(g.double().cpu().numpy().ravel() - ref) / np.linalg.norm(ref))
+    errs = {}
+    for form in ("auto", "levels"):
+        p = api.Problem.from_workload(w, form=form)
+        for acc in (("f32", "bf16", "bf16_kahan") if form == "auto" else ("f32",)):
+            g, _ = p.gradient_probed(vel0, wav, d_obs, api.ProbeSpec(kind="gaussian", r=16, T=32, seed=w.seed, acc=acc))
+            errs[f"{p.form}_{acc}"] = rel(g)
+            p.release()
+    p = api.Problem.from_workload(w)
+    v = vel0.clone().requires_grad_(True)
+    loss = 0.5 * ((modeling(v, p, wav, api.ProbeSpec(kind="gaussian", r=16, T=32, seed=w.seed)) - d_obs).double() ** 2).sum()
+    loss.backward()
+    gv_ref = ref * (-2.0 / w.vel0.astype(np.float64).ravel() ** 3)
+    ag = float(np.linalg.norm(v.grad.double().cpu().numpy().ravel() - gv_ref) / np.linalg.norm(gv_ref))
+    out["config4_precision"] = {
+        "case": "2 of the 8 shots (first and last), 801x301, nt=2500, r=16 Gaussian, same probes as the FP64 oracle",
+        "probed_gradient_rel_l2": errs, "autograd_backward_rel_l2": ag,
+        "misfit_rel": abs(float(loss.detach()) - J) / J, "oracle_seconds": t_or}
+    return out
+
+
 def wl_seed():
     from paper_2104_00794_gb300 import workloads as wl
     return wl.DEFAULT_SEED
@@ -461,6 +549,11 @@ def main():
                "kind": "oracle", "sample": f"probed gradient, {sample}", "seconds": tc}
         pc.release()
 
+    # ---- the 2-D configurations and config 4's precision (N = 1)
+    configs_2d = None
+    if not args.no_2d and args.workload == "config3" and world == 1:
+        configs_2d = run_2d(args)
+
     # ---- serving: Poisson stream of mixed-size shot-gradient requests
     serving = None
     if not args.no_serve and args.workload == "config3":
@@ -500,6 +593,7 @@ def main():
             "cpu_baseline": cpu,
             "err_vs_fp64": err,
             "serving": serving,
+            "configs_2d": configs_2d,
         }
         print(json.dumps(line), flush=True)
     reps.close()

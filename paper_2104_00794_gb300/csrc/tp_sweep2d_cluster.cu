@@ -343,82 +343,116 @@ __global__ void __launch_bounds__(C2_THREADS, 1) sweep2d_cluster(C2Args a) {
                                     : bf4(*reinterpret_cast<const uint2*>(re[r] + 4 * cu));
       };
       if (ra < rb) {
-        float4 q[2 * R + 1], eq[2 * R + 1];
+        // the queue is circular: row r + d of block row j sits in slot
+        // (j + R + d) mod NQ, so whole blocks of NQ rows need no register moves
+        constexpr int NQ = 2 * R + 1;
+        float4 q[NQ], eq[NQ];
 #pragma unroll
         for (int k = 0; k < 2 * R; ++k) {
           q[k] = ld_u(ra - R + k);
           if (COMP) eq[k] = ld_e(ra - R + k);
         }
         const float* c2col = a.c2 + (long long)(z0 + H) * px + HX + 4 * cu;
-#pragma unroll(2 * R + 1)
-        for (int r = ra; r < rb; ++r) {
-          q[2 * R] = ld_u(r + R);
-          if (COMP) eq[2 * R] = ld_e(r + R);
-          const uint32_t ou = (uint32_t)(r * sx + 4 + 4 * cu);
-          const float4 xl = lds4(sUc + (ou - 4) * 4u), xr = lds4(sUc + (ou + 4) * 4u), xc = q[R];
-          const float4 c1 = lds4(sUn + ou * 4u);  // previous level
-          const float4 cq = __ldg(reinterpret_cast<const float4*>(c2col + (long long)r * px));
-          const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-          float o[4], en[4] = {0.f, 0.f, 0.f, 0.f};
-          if (!COMP) {
-            // centred form, the per-step 2-D sweep's operations in its order
-            float2 s2[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+        for (int r0 = ra; r0 < rb; r0 += NQ) {
 #pragma unroll
-            for (int k = 1; k <= R; ++k) {
-              const float4 zp = q[R + k], zm = q[R - k];
-              const float2 wk = f2(a.W.w[k], a.W.w[k]);
+          for (int j = 0; j < NQ; ++j) {
+            const int r = r0 + j;
+            if (r < rb) {
+              q[(j + 2 * R) % NQ] = ld_u(r + R);
+              if (COMP) eq[(j + 2 * R) % NQ] = ld_e(r + R);
+              const uint32_t ou = (uint32_t)(r * sx + 4 + 4 * cu);
+              const float4 xl = lds4(sUc + (ou - 4) * 4u), xr = lds4(sUc + (ou + 4) * 4u), xc = q[(j + R) % NQ];
+              const float4 c1 = lds4(sUn + ou * 4u);  // previous level
+              const float4 cq = __ldg(reinterpret_cast<const float4*>(c2col + (long long)r * px));
+              const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
+              float o[4], en[4] = {0.f, 0.f, 0.f, 0.f};
+              if (!COMP) {
+                // centred form, the per-step 2-D sweep's operations in its order
+                float2 s2[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
 #pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int pp = 2 * h;
-                const float2 cv = f2(v[4 + pp], v[5 + pp]);
-                const float2 xs = __fadd2_rn(f2(v[4 + pp + k], v[5 + pp + k]), f2(v[4 + pp - k], v[5 + pp - k]));
-                const float2 zs = __fadd2_rn(h ? f2(zp.z, zp.w) : f2(zp.x, zp.y), h ? f2(zm.z, zm.w) : f2(zm.x, zm.y));
-                s2[h] = __ffma2_rn(wk, __ffma2_rn(m4, cv, __fadd2_rn(xs, zs)), s2[h]);
+                for (int k = 1; k <= R; ++k) {
+                  const float4 zp = q[(j + R + k) % NQ], zm = q[(j + R - k) % NQ];
+                  const float2 wk = f2(a.W.w[k], a.W.w[k]);
+#pragma unroll
+                  for (int h = 0; h < 2; ++h) {
+                    const int pp = 2 * h;
+                    const float2 cv = f2(v[4 + pp], v[5 + pp]);
+                    const float2 xs = __fadd2_rn(f2(v[4 + pp + k], v[5 + pp + k]), f2(v[4 + pp - k], v[5 + pp - k]));
+                    const float2 zs = __fadd2_rn(h ? f2(zp.z, zp.w) : f2(zp.x, zp.y), h ? f2(zm.z, zm.w) : f2(zm.x, zm.y));
+                    s2[h] = __ffma2_rn(wk, __ffma2_rn(m4, cv, __fadd2_rn(xs, zs)), s2[h]);
+                  }
+                }
+                // new = c2 S + (2u - u_prev); 2u is exact, so the FMA rounds 2u - u_prev once, as a subtraction
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int pp = 2 * h;
+                  const float2 t = __ffma2_rn(f2(2.f, 2.f), f2(v[4 + pp], v[5 + pp]),
+                                              f2(-comp4(c1, pp), -comp4(c1, pp + 1)));
+                  const float2 r2 = __ffma2_rn(f2(comp4(cq, pp), comp4(cq, pp + 1)), s2[h], t);
+                  o[pp] = r2.x;
+                  o[pp + 1] = r2.y;
+                }
+              } else {
+                // double-float levels: U = u + e.  S(u) in the difference form, S(e)
+                // in the centred form (e is a few ulp of u: its rounding is negligible)
+                const float4 el = bf4(lds2(sEc + (ou - 4) * 2u)), er = bf4(lds2(sEc + (ou + 4) * 2u)), ec = eq[(j + R) % NQ];
+                const float ve[12] = {el.x, el.y, el.z, el.w, ec.x, ec.y, ec.z, ec.w, er.x, er.y, er.z, er.w};
+                const float4 e1 = bf4(lds2(sEn + ou * 2u));
+                // two points per packed fp32x2 instruction (each lane the scalar
+                // operation of the unpacked form, in the same order)
+                float2 su[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, se[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll
+                for (int k = 1; k <= R; ++k) {
+                  const float4 zp = q[(j + R + k) % NQ], zm = q[(j + R - k) % NQ], ezp = eq[(j + R + k) % NQ],
+                               ezm = eq[(j + R - k) % NQ];
+                  const float2 wk = f2(a.W.w[k], a.W.w[k]);
+#pragma unroll
+                  for (int h = 0; h < 2; ++h) {
+                    const int pp = 2 * h;
+                    const float2 nu = f2(-v[4 + pp], -v[5 + pp]);
+                    const float2 dxp = __fadd2_rn(f2(v[4 + pp + k], v[5 + pp + k]), nu);
+                    const float2 dxm = __fadd2_rn(f2(v[4 + pp - k], v[5 + pp - k]), nu);
+                    const float2 dzp = __fadd2_rn(h ? f2(zp.z, zp.w) : f2(zp.x, zp.y), nu);
+                    const float2 dzm = __fadd2_rn(h ? f2(zm.z, zm.w) : f2(zm.x, zm.y), nu);
+                    su[h] = __ffma2_rn(wk, __fadd2_rn(__fadd2_rn(dxp, dxm), __fadd2_rn(dzp, dzm)), su[h]);
+                    const float2 xe = __fadd2_rn(f2(ve[4 + pp + k], ve[5 + pp + k]), f2(ve[4 + pp - k], ve[5 + pp - k]));
+                    const float2 ze = __fadd2_rn(h ? f2(ezp.z, ezp.w) : f2(ezp.x, ezp.y), h ? f2(ezm.z, ezm.w) : f2(ezm.x, ezm.y));
+                    se[h] = __ffma2_rn(wk, __ffma2_rn(m4, f2(ve[4 + pp], ve[5 + pp]), __fadd2_rn(xe, ze)), se[h]);
+                  }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int pp = 2 * h;
+                  const float2 two = f2(2.f, 2.f);
+                  const float2 uu = f2(v[4 + pp], v[5 + pp]), ee = f2(ve[4 + pp], ve[5 + pp]);
+                  const float2 cm = f2(-comp4(c1, pp), -comp4(c1, pp + 1));
+                  const float2 em = f2(-comp4(e1, pp), -comp4(e1, pp + 1));
+                  const float2 cc2 = f2(comp4(cq, pp), comp4(cq, pp + 1));
+                  // 2u - u_prev exactly (TwoSum), then the small terms, then TwoSum again
+                  const float2 u2 = __fmul2_rn(two, uu);
+                  const float2 av = __fadd2_rn(u2, cm);
+                  const float2 bb = __fadd2_rn(av, f2(-u2.x, -u2.y));
+                  const float2 ea = __fadd2_rn(__fadd2_rn(u2, f2(-(av.x - bb.x), -(av.y - bb.y))), __fadd2_rn(cm, f2(-bb.x, -bb.y)));
+                  const float2 b = __ffma2_rn(cc2, __fadd2_rn(su[h], se[h]), __ffma2_rn(two, ee, em));
+                  const float2 bt = __fadd2_rn(b, ea);
+                  const float2 sm = __fadd2_rn(av, bt);
+                  const float2 b2 = __fadd2_rn(sm, f2(-av.x, -av.y));
+                  const float2 er2 = __fadd2_rn(__fadd2_rn(av, f2(-(sm.x - b2.x), -(sm.y - b2.y))), __fadd2_rn(bt, f2(-b2.x, -b2.y)));
+                  o[pp] = sm.x;
+                  o[pp + 1] = sm.y;
+                  en[pp] = er2.x;
+                  en[pp + 1] = er2.y;
+                }
               }
-            }
-            const float s4[4] = {s2[0].x, s2[0].y, s2[1].x, s2[1].y};
+              if (4 * cu + 3 >= nx) {  // columns past the grid stay zero
 #pragma unroll
-            for (int pp = 0; pp < 4; ++pp) o[pp] = fmaf(comp4(cq, pp), s4[pp], 2.0f * v[4 + pp] - comp4(c1, pp));
-          } else {
-            // double-float levels: U = u + e.  S(u) in the difference form, S(e)
-            // in the centred form (e is a few ulp of u: its rounding is negligible)
-            const float4 el = bf4(lds2(sEc + (ou - 4) * 2u)), er = bf4(lds2(sEc + (ou + 4) * 2u)), ec = eq[R];
-            const float ve[12] = {el.x, el.y, el.z, el.w, ec.x, ec.y, ec.z, ec.w, er.x, er.y, er.z, er.w};
-            const float4 e1 = bf4(lds2(sEn + ou * 2u));
-            float su[4] = {0.f, 0.f, 0.f, 0.f}, se[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int k = 1; k <= R; ++k) {
-              const float4 zp = q[R + k], zm = q[R - k], ezp = eq[R + k], ezm = eq[R - k];
-              const float wk = a.W.w[k];
-#pragma unroll
-              for (int pp = 0; pp < 4; ++pp) {
-                const float u0 = v[4 + pp];
-                const float t = ((v[4 + pp + k] - u0) + (v[4 + pp - k] - u0)) + ((comp4(zp, pp) - u0) + (comp4(zm, pp) - u0));
-                su[pp] = fmaf(wk, t, su[pp]);
-                const float te = (ve[4 + pp + k] + ve[4 + pp - k]) + (comp4(ezp, pp) + comp4(ezm, pp));
-                se[pp] = fmaf(wk, fmaf(-4.f, ve[4 + pp], te), se[pp]);
+                for (int pp = 0; pp < 4; ++pp)
+                  if (4 * cu + pp >= nx) o[pp] = en[pp] = 0.f;
               }
+              // the new value over the previous level (own points: no other thread reads them in this step)
+              *reinterpret_cast<float4*>(Un + (size_t)r * sx + 4 + 4 * cu) = make_float4(o[0], o[1], o[2], o[3]);
+              if (COMP) st_bf4(En + (size_t)r * sx + 4 + 4 * cu, make_float4(en[0], en[1], en[2], en[3]));
             }
-#pragma unroll
-            for (int pp = 0; pp < 4; ++pp) {
-              float ea;
-              const float av = two_sum(2.0f * v[4 + pp], -comp4(c1, pp), &ea);  // 2u - u_prev, exactly
-              const float b = fmaf(comp4(cq, pp), su[pp] + se[pp], 2.0f * ve[4 + pp] - comp4(e1, pp));
-              o[pp] = two_sum(av, b + ea, &en[pp]);
-            }
-          }
-          if (4 * cu + 3 >= nx) {  // columns past the grid stay zero
-#pragma unroll
-            for (int pp = 0; pp < 4; ++pp)
-              if (4 * cu + pp >= nx) o[pp] = en[pp] = 0.f;
-          }
-          // the new value over the previous level (own points: no other thread reads them in this step)
-          *reinterpret_cast<float4*>(Un + (size_t)r * sx + 4 + 4 * cu) = make_float4(o[0], o[1], o[2], o[3]);
-          if (COMP) st_bf4(En + (size_t)r * sx + 4 + 4 * cu, make_float4(en[0], en[1], en[2], en[3]));
-#pragma unroll
-          for (int k = 0; k < 2 * R; ++k) {
-            q[k] = q[k + 1];
-            if (COMP) eq[k] = eq[k + 1];
           }
         }
       }
