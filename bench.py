@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-nt", type=int, default=48, help="time levels of the bounded CPU sample")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (p50/p99) leg")
-    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--no-2d", action="store_true",
                     help="skip the 2-D configurations (1, 2, 4) and config 4's precision leg (N = 1 only)")
     return ap.parse_args()
@@ -211,58 +211,78 @@ def run_reference(args, rank: int):
 
 
 # ------------------------------------------------------------------ serving leg
+# Request shapes of the serving mix (config 5): 2-D grids 201^2 .. 1001x401 and
+# 3-D 128^3 .. 320^3, nt 1000-4000, r in {8, 16, 32}, order 8.  Requests of one
+# shape differ in their source position, their model and their data.
+SERVE_SHAPES = [("2d", (201, 201), 1000, 8), ("2d", (601, 301), 2000, 16), ("2d", (1001, 401), 3000, 16),
+                ("2d", (401, 401), 4000, 32), ("3d", 128, 1000, 8), ("3d", 192, 2000, 16), ("3d", 256, 2000, 32),
+                ("3d", 320, 1000, 16)]
+
+
 def serving_mix(n: int, seed: int):
-    """Request mix: 2-D grids 201^2 .. 1001x401 and 3-D 128^3 .. 320^3, nt in
-    [1000, 4000], r in {8, 16, 32}, order 8, probed gradients (one shot)."""
+    """n probed-gradient requests (one shot each) drawn from SERVE_SHAPES.
+    Per shape one base model (seeded, on the host); per request a source
+    position, a model scaled by a factor in [0.97, 1] of the base and
+    synthetic observed data, made on the device."""
+    import torch
+    from paper_2104_00794_gb300 import api, serve
     from paper_2104_00794_gb300 import workloads as wl
     rng = np.random.default_rng(seed)
-    out = []
-    for i in range(n):
-        nt = int(rng.integers(1000, 4001))
-        r = int(rng.choice([8, 16, 32]))
-        if rng.uniform() < 0.5:
-            nx = int(rng.integers(201, 1002))
-            nz = int(rng.integers(201, min(nx, 401) + 1))
-            w = wl.small_2d(nx=nx, nz=nz, nt=nt, order=8, r=r, probe_kind="rademacher", h=10.0, dt=1e-3,
+    bases = []
+    for i, (dim, size, nt, r) in enumerate(SERVE_SHAPES):
+        if dim == "2d":
+            w = wl.small_2d(nx=size[0], nz=size[1], nt=nt, order=8, r=r, probe_kind="rademacher", h=10.0, dt=1e-3,
                             f0=10.0, seed=seed + i)
         else:
-            m = int(rng.integers(128, 321))
-            w = wl.config3(n=m, nt=nt, r=r, seed=seed + i, rec_stride=2)
-        out.append(w)
-    return out
+            w = wl.config3(n=size, nt=nt, r=r, seed=seed + i, rec_stride=2)
+        bases.append((w, torch.tensor(np.ascontiguousarray(w.vel0), device="cuda"),
+                      torch.tensor(np.ascontiguousarray(w.wavelet), device="cuda")))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    reqs = []
+    for i in range(n):
+        w, vel, wav = bases[int(rng.integers(len(bases)))]
+        src = int(w.src[0, 0])
+        if w.ndim == 2:
+            src = src - (src % w.nx) + int(rng.integers(w.nx // 8, w.nx - w.nx // 8))
+        else:
+            plane = w.nx * w.ny
+            src = (src // plane) * plane + int(rng.integers(w.ny // 4, 3 * w.ny // 4)) * w.nx + \
+                int(rng.integers(w.nx // 4, 3 * w.nx // 4))
+        vmax = float(w.vel0.max())
+        p = api.Problem(w.ndim, w.nx, w.ny, w.nz, w.h, w.dt, w.nt, w.order, [[src]], w.rec[:1], vmax=vmax)
+        v = vel * (1.0 - 0.03 * float(rng.uniform()))
+        d_obs = 1e-3 * torch.randn((1, w.nt, w.rec.shape[1]), device="cuda", generator=gen)
+        probe = api.ProbeSpec(kind="rademacher", r=w.r, T=32, seed=w.seed)
+        reqs.append((serve.GradientJob(p, v, wav, d_obs, probe), 2.0 * w.N * w.nt))
+    return reqs
 
 
 def run_serving(args, rank):
     import torch
-    from paper_2104_00794_gb300 import api, serve
-    mix = serving_mix(args.serve_requests, seed=wl_seed() + 17 * rank)
-    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")  # copies (inputs may be read-only)
-    jobs = []
-    for w in mix:
-        p = api.Problem.from_workload(w)
-        dobs = p.forward(dev(w.vel_true), dev(w.wavelet)).clone()
-        p.release()
-        jobs.append(serve.GradientJob(p, dev(w.vel0), dev(w.wavelet), dobs,
-                                      api.ProbeSpec(kind="rademacher", r=w.r, T=32, seed=w.seed)))
+    from paper_2104_00794_gb300 import serve
+    jobs = serving_mix(args.serve_requests, seed=wl_seed() + 17 * rank)
     torch.cuda.synchronize()
-    work = [2.0 * w.N * w.nt for w in mix]
+    work = [wk for _, wk in jobs]
     # service-time estimate from the 3-D rate, arrival rate for ~75 % busy
     est = float(np.mean(work)) / 150e9
     rng = np.random.default_rng(99 + rank)
-    arrivals = np.cumsum(rng.exponential(est / 0.75, size=len(mix)))
+    arrivals = np.cumsum(rng.exponential(est / 0.75, size=len(jobs)))
     arrivals -= arrivals[0]
-    reqs = [serve.Request(i, float(arrivals[i]), jobs[i].footprint(), work[i], jobs[i]) for i in range(len(mix))]
+    reqs = [serve.Request(i, float(arrivals[i]), j.footprint(), work[i], j) for i, (j, _) in enumerate(jobs)]
     budget = int(80e9)
-    sched = serve.Scheduler(budget, max_slots=6)
-    ex = serve.GpuExecutor(use_graphs=True)
+    sched = serve.Scheduler(budget, max_slots=8)
+    ex = serve.GpuExecutor(cache_bytes=int(60e9))
     t0 = time.perf_counter()
     serve.run(reqs, sched, ex.start, ex.poll)
     torch.cuda.synchronize()
     makespan = time.perf_counter() - t0
-    s = serve.summarize(reqs, makespan)
+    s = serve.summarize(reqs, makespan, captured=ex.captured)
     s.update({"slots_max": sched.max_slots, "peak_concurrent": sched.peak_active, "budget_bytes": budget,
-              "peak_bytes": sched.peak_used, "mix": "2-D 201^2..1001x401 and 3-D 128^3..320^3, nt 1000-4000, r 8/16/32",
-              "arrivals": "Poisson, rate for ~75 % busy", "graphs": True})
+              "peak_bytes": sched.peak_used, "shapes": len(SERVE_SHAPES),
+              "mix": "2-D 201^2..1001x401 and 3-D 128^3..320^3, nt 1000-4000, r 8/16/32 (8 shapes)",
+              "arrivals": "Poisson, rate for ~75 % busy"})
+    s.update(ex.stats())
     return s
 
 

@@ -146,6 +146,8 @@ struct Plan {
   size_t bytes = 0;
   size_t o_scal = 0, o_part = 0, o_c2 = 0, o_f = 0, o_P = 0, o_V = 0, o_Q = 0, o_d = 0, o_soff = 0, o_roff = 0,
          o_cs = 0, o_cr = 0, o_qbar = 0, o_gacc = 0, o_sacc = 0, o_conv = 0, o_w = 0;
+  // deterministic injection groups of the sources and of the receivers
+  size_t o_salone = 0, o_ralone = 0, o_sshared = 0, o_rshared = 0, o_sn = 0, o_rn = 0;
   long long nf = 0;  // fields in the wavefield block
   // probed state (Q, then the forward accumulators): offsets inside the state
   // buffer, which tp_gradient_probed places at o_state of its workspace
@@ -227,6 +229,12 @@ tp_status make_plan(int op, const tp_grid* g, const tp_geom* geo, const tp_probe
   P->o_roff = take(cur, (size_t)ns * P->nrec * sizeof(long long));
   P->o_cs = take(cur, (size_t)ns * P->nsrc * sizeof(float));
   P->o_cr = take(cur, (size_t)ns * P->nrec * sizeof(float));
+  P->o_salone = take(cur, (size_t)ns * P->nsrc);
+  P->o_ralone = take(cur, (size_t)ns * P->nrec);
+  P->o_sshared = take(cur, (size_t)ns * P->nsrc * sizeof(int));
+  P->o_rshared = take(cur, (size_t)ns * P->nrec * sizeof(int));
+  P->o_sn = take(cur, (size_t)ns * sizeof(int));
+  P->o_rn = take(cur, (size_t)ns * sizeof(int));
   P->o_c2 = take(cur, fb);
   P->form = g->form;
   P->comp = g->form == TP_FORM_COMPENSATED;
@@ -335,6 +343,13 @@ tp_status setup(const Ctx& c, const tp_grid* g, const tp_geom* geo, const float*
                          c.at<float>(P.o_cs), c.err(), c.st));
   TRY(launch_prep_points(P.L, P.W, geo->rec, (long long)P.nshots * P.nrec, vel, dt2, c.at<long long>(P.o_roff),
                          c.at<float>(P.o_cr), c.err(), c.st));
+  // injection groups; the wavefield block (at least one field per shot, zeroed
+  // by every operation after the set-up) serves as the count scratch
+  int* cnt = c.at<int>(P.o_f);
+  TRY(launch_point_groups(c.at<long long>(P.o_soff), P.nsrc, P.nshots, P.L.field, cnt, c.at<unsigned char>(P.o_salone),
+                          c.at<int>(P.o_sshared), c.at<int>(P.o_sn), c.st));
+  TRY(launch_point_groups(c.at<long long>(P.o_roff), P.nrec, P.nshots, P.L.field, cnt, c.at<unsigned char>(P.o_ralone),
+                          c.at<int>(P.o_rshared), c.at<int>(P.o_rn), c.st));
   float vmax = g->vmax;
   if (!(vmax > 0.f)) {
     TRY(launch_vmax(vel, (long long)g->nx * g->ny * g->nz, &c.scal()->vmax_bits, c.st));
@@ -377,6 +392,12 @@ tp_status point(const Ctx& c, const float* samp, long long samp_ss, const long l
   a.field_samp = samp; a.samp_ss = samp_ss; a.samp_off = soff; a.nsamp = samp ? nsamp : 0;
   a.samp_out = out; a.samp_out_ss = out_ss;
   a.field_inj = inj; a.inj_ss = inj_ss; a.inj_off = ioff; a.inj_coef = icoef; a.ninj = inj ? ninj : 0;
+  if (inj) {  // the groups of the set whose offsets ioff are
+    const bool src = ioff == c.at<long long>(c.P.o_soff);
+    a.inj_alone = c.at<unsigned char>(src ? c.P.o_salone : c.P.o_ralone);
+    a.inj_shared = c.at<int>(src ? c.P.o_sshared : c.P.o_rshared);
+    a.inj_nshared = c.at<int>(src ? c.P.o_sn : c.P.o_rn);
+  }
   if (inj && c.P.form == TP_FORM_INCREMENT) {  // sources enter the increment as well as the new level
     a.field_inj2 = c.ptr(inc_fam(c.P), 0);
     a.inj2_ss = c.ss(inc_fam(c.P));

@@ -177,6 +177,9 @@ cudaError_t launch_prep_points(const Layout& L, const Weights& W, const int64_t*
 //   sample: samp_out[s][t_s][j] = field_samp[s][samp_off[s][j]]           (j < nsamp)
 //   inject: field_inj[s][inj_off[s][k]] += inj_coef[s][k] * inj_val[s][t_i][k]  (k < ninj)
 //   srcacc (optional): acc[s][j] += sampled value * acc_val[s][t_a][j]
+// Injection is deterministic: entries alone at their node (inj_alone[s][k])
+// are added by their own thread, the others (inj_shared[s][0 .. inj_nshared[s]),
+// in index order) by one thread per shot, one after the other.
 struct PointArgs {
   int nshots;
   const float* field_samp; long long samp_ss;
@@ -185,9 +188,14 @@ struct PointArgs {
   float* field_inj2; long long inj2_ss;  // optional second target (the increment field)
   const long long* inj_off; const float* inj_coef; int ninj;
   const float* inj_val; long long inj_val_ss;  // already offset to t
+  const unsigned char* inj_alone; const int* inj_shared; const int* inj_nshared;
   double* acc; const float* acc_val; long long acc_val_ss;  // may be null
 };
 cudaError_t launch_point(const PointArgs& a, cudaStream_t s);
+// alone / shared / nshared of a point set (per_shot entries per shot) from the
+// padded offsets; cnt_scratch: nshots * field ints of scratch
+cudaError_t launch_point_groups(const long long* off, int per_shot, int nshots, long long field, int* cnt_scratch,
+                                unsigned char* alone, int* shared, int* nshared, cudaStream_t s);
 
 cudaError_t launch_probes(int kind, int nt, int r, uint64_t seed, int shot0, int nshots,
                           const float* Z_user, float* Q, cudaStream_t s);

@@ -51,6 +51,22 @@ __global__ void prep_points_kernel(Layout L, Weights W, const int64_t* __restric
   }
 }
 
+__device__ __forceinline__ void inject_one(const PointArgs& a, int s, int k) {
+  const long long k2 = (long long)s * a.ninj + k;
+  const long long o = a.inj_off[k2];
+  if (o < 0) return;
+  const float v = a.inj_coef[k2] * a.inj_val[s * a.inj_val_ss + k];
+  float* f = a.field_inj + s * a.inj_ss + o;
+  *f = *f + v;
+  if (a.field_inj2) {
+    float* f2 = a.field_inj2 + s * a.inj2_ss + o;
+    *f2 = *f2 + v;
+  }
+}
+
+// Sampling threads, then one thread per injection entry that is alone at its
+// node, then one thread per shot that adds the entries sharing nodes, in
+// index order: every node's sum has a fixed order (deterministic results).
 __global__ void point_kernel(PointArgs a) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long ns = (long long)a.nshots * a.nsamp;
@@ -63,15 +79,59 @@ __global__ void point_kernel(PointArgs a) {
     return;
   }
   const long long k2 = i - ns;
-  if (k2 < (long long)a.nshots * a.ninj) {
-    const int s = (int)(k2 / a.ninj), k = (int)(k2 % a.ninj);
-    const long long o = a.inj_off[k2];
-    if (o >= 0) {
-      const float v = a.inj_coef[k2] * a.inj_val[s * a.inj_val_ss + k];
-      atomicAdd(a.field_inj + s * a.inj_ss + o, v);
-      if (a.field_inj2) atomicAdd(a.field_inj2 + s * a.inj2_ss + o, v);
-    }
+  const long long ni = (long long)a.nshots * a.ninj;
+  if (k2 < ni) {
+    if (a.inj_alone[k2]) inject_one(a, (int)(k2 / a.ninj), (int)(k2 % a.ninj));
+    return;
   }
+  const long long s = k2 - ni;
+  if (a.ninj > 0 && s < a.nshots) {
+    const int nd = a.inj_nshared[s];
+    for (int d = 0; d < nd; ++d) inject_one(a, (int)s, a.inj_shared[s * a.ninj + d]);
+  }
+}
+
+// Nodes with more than one entry of a point set (counts over the padded
+// field of each shot; `cnt` is zero on entry)
+__global__ void point_count_kernel(const long long* __restrict__ off, long long n, int per_shot, long long field,
+                                   int* cnt) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long o = off[k];
+    if (o >= 0) atomicAdd(cnt + (k / per_shot) * field + o, 1);
+  }
+}
+
+// One block per shot: alone[k] for every entry, and the entries whose node
+// has several, compacted in index order into shared[shot][..], nshared[shot]
+__global__ void __launch_bounds__(256) point_group_kernel(const long long* __restrict__ off, int per_shot,
+                                                          long long field, const int* __restrict__ cnt,
+                                                          unsigned char* alone, int* shared, int* nshared) {
+  __shared__ int warp_cnt[8];
+  __shared__ int base_cnt;
+  const int s = blockIdx.x, tid = threadIdx.x;
+  if (tid == 0) base_cnt = 0;
+  __syncthreads();
+  for (int b = 0; b < per_shot; b += 256) {
+    const int k = b + tid;
+    bool dup = false;
+    if (k < per_shot) {
+      const long long o = off[(long long)s * per_shot + k];
+      const bool one = o < 0 || cnt[(long long)s * field + o] == 1;
+      alone[(long long)s * per_shot + k] = one ? 1 : 0;
+      dup = !one;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, dup);
+    if ((tid & 31) == 0) warp_cnt[tid >> 5] = __popc(m);
+    __syncthreads();
+    int before = base_cnt;
+    for (int w = 0; w < (tid >> 5); ++w) before += warp_cnt[w];
+    if (dup) shared[(long long)s * per_shot + before + __popc(m & ((1u << (tid & 31)) - 1u))] = k;
+    __syncthreads();
+    if (tid == 0)
+      for (int w = 0; w < 8; ++w) base_cnt += warp_cnt[w];
+    __syncthreads();
+  }
+  if (tid == 0) nshared[s] = base_cnt;
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014): the n-th output of a generator whose
@@ -291,8 +351,22 @@ cudaError_t launch_prep_points(const Layout& L, const Weights& W, const int64_t*
   return cudaGetLastError();
 }
 
+cudaError_t launch_point_groups(const long long* off, int per_shot, int nshots, long long field, int* cnt_scratch,
+                                unsigned char* alone, int* shared, int* nshared, cudaStream_t s) {
+  prof_before(5, s);
+  cudaError_t e = cudaMemsetAsync(cnt_scratch, 0, (size_t)nshots * field * sizeof(int), s);
+  if (e == cudaSuccess) {
+    const long long n = (long long)nshots * per_shot;
+    point_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, n, per_shot, field, cnt_scratch);
+    point_group_kernel<<<nshots, 256, 0, s>>>(off, per_shot, field, cnt_scratch, alone, shared, nshared);
+    e = cudaGetLastError();
+  }
+  prof_after(5, s);
+  return e;
+}
+
 cudaError_t launch_point(const PointArgs& a, cudaStream_t s) {
-  const long long n = (long long)a.nshots * (a.nsamp + a.ninj);
+  const long long n = (long long)a.nshots * (a.nsamp + a.ninj) + (a.ninj > 0 ? a.nshots : 0);
   if (n == 0) return cudaSuccess;
   prof_before(3, s);
   point_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
