@@ -356,17 +356,18 @@ def run_2d(args):
     for form in ("auto", "levels"):
         p = api.Problem.from_workload(w, form=form)
         for acc in (("f32", "bf16", "bf16_kahan") if form == "auto" else ("f32",)):
-            g, _ = p.gradient_probed(vel0, wav, d_obs, api.ProbeSpec(kind="gaussian", r=16, T=32, seed=w.seed, acc=acc))
+            g, _ = p.gradient_probed(vel0, wav, d_obs, api.ProbeSpec(kind="gaussian", r=16, T=w.T, seed=w.seed, acc=acc))
             errs[f"{p.form}_{acc}"] = rel(g)
             p.release()
     p = api.Problem.from_workload(w)
     v = vel0.clone().requires_grad_(True)
-    loss = 0.5 * ((modeling(v, p, wav, api.ProbeSpec(kind="gaussian", r=16, T=32, seed=w.seed)) - d_obs).double() ** 2).sum()
+    loss = 0.5 * ((modeling(v, p, wav, api.ProbeSpec(kind="gaussian", r=16, T=w.T, seed=w.seed)) - d_obs).double() ** 2).sum()
     loss.backward()
     gv_ref = ref * (-2.0 / w.vel0.astype(np.float64).ravel() ** 3)
     ag = float(np.linalg.norm(v.grad.double().cpu().numpy().ravel() - gv_ref) / np.linalg.norm(gv_ref))
     out["config4_precision"] = {
-        "case": "2 of the 8 shots (first and last), 801x301, nt=2500, r=16 Gaussian, same probes as the FP64 oracle",
+        "case": (f"2 of the 8 shots (first and last), 801x301, nt=2500, r=16 Gaussian, T={w.T}, "
+                 "same probes as the FP64 oracle"),
         "probed_gradient_rel_l2": errs, "autograd_backward_rel_l2": ag,
         "misfit_rel": abs(float(loss.detach()) - J) / J, "oracle_seconds": t_or}
     return out

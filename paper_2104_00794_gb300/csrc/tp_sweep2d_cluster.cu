@@ -393,8 +393,9 @@ __global__ void __launch_bounds__(C2_THREADS, 1) sweep2d_cluster(C2Args a) {
                   o[pp + 1] = r2.y;
                 }
               } else {
-                // double-float levels: U = u + e.  S(u) in the difference form, S(e)
-                // in the centred form (e is a few ulp of u: its rounding is negligible)
+                // double-float levels: U = u + e.  S(u) in the difference form for
+                // k = 1, 2 and the centred form for the small weights k = 3, 4; S(e) in
+                // the centred form (e is a few ulp of u: its rounding is negligible)
                 const float4 el = bf4(lds2(sEc + (ou - 4) * 2u)), er = bf4(lds2(sEc + (ou + 4) * 2u)), ec = eq[(j + R) % NQ];
                 const float ve[12] = {el.x, el.y, el.z, el.w, ec.x, ec.y, ec.z, ec.w, er.x, er.y, er.z, er.w};
                 const float4 e1 = bf4(lds2(sEn + ou * 2u));
@@ -409,12 +410,22 @@ __global__ void __launch_bounds__(C2_THREADS, 1) sweep2d_cluster(C2Args a) {
 #pragma unroll
                   for (int h = 0; h < 2; ++h) {
                     const int pp = 2 * h;
-                    const float2 nu = f2(-v[4 + pp], -v[5 + pp]);
-                    const float2 dxp = __fadd2_rn(f2(v[4 + pp + k], v[5 + pp + k]), nu);
-                    const float2 dxm = __fadd2_rn(f2(v[4 + pp - k], v[5 + pp - k]), nu);
-                    const float2 dzp = __fadd2_rn(h ? f2(zp.z, zp.w) : f2(zp.x, zp.y), nu);
-                    const float2 dzm = __fadd2_rn(h ? f2(zm.z, zm.w) : f2(zm.x, zm.y), nu);
-                    su[h] = __ffma2_rn(wk, __fadd2_rn(__fadd2_rn(dxp, dxm), __fadd2_rn(dzp, dzm)), su[h]);
+                    const float2 xp = f2(v[4 + pp + k], v[5 + pp + k]), xm = f2(v[4 + pp - k], v[5 + pp - k]);
+                    const float2 zpp = h ? f2(zp.z, zp.w) : f2(zp.x, zp.y), zmm = h ? f2(zm.z, zm.w) : f2(zm.x, zm.y);
+                    if (k <= 2) {
+                      // the two heavy weights: per-neighbour differences, exact
+                      // for neighbours within a factor two of the centre
+                      const float2 nu = f2(-v[4 + pp], -v[5 + pp]);
+                      const float2 dxp = __fadd2_rn(xp, nu), dxm = __fadd2_rn(xm, nu);
+                      const float2 dzp = __fadd2_rn(zpp, nu), dzm = __fadd2_rn(zmm, nu);
+                      su[h] = __ffma2_rn(wk, __fadd2_rn(__fadd2_rn(dxp, dxm), __fadd2_rn(dzp, dzm)), su[h]);
+                    } else {
+                      // |w_3|, |w_4| < 0.03: the centred form's rounding is a few
+                      // hundredths of an ulp of u here
+                      su[h] = __ffma2_rn(wk, __ffma2_rn(m4, f2(v[4 + pp], v[5 + pp]),
+                                                        __fadd2_rn(__fadd2_rn(xp, xm), __fadd2_rn(zpp, zmm))),
+                                         su[h]);
+                    }
                     const float2 xe = __fadd2_rn(f2(ve[4 + pp + k], ve[5 + pp + k]), f2(ve[4 + pp - k], ve[5 + pp - k]));
                     const float2 ze = __fadd2_rn(h ? f2(ezp.z, ezp.w) : f2(ezp.x, ezp.y), h ? f2(ezm.z, ezm.w) : f2(ezm.x, ezm.y));
                     se[h] = __ffma2_rn(wk, __ffma2_rn(m4, f2(ve[4 + pp], ve[5 + pp]), __fadd2_rn(xe, ze)), se[h]);

@@ -176,8 +176,8 @@ def config1(seed: int = DEFAULT_SEED) -> Workload:
     """2-D 101x101 at 10 m, two layers 1.5/2.5 km/s (interface at 250 m, so
     that its reflection arrives at about 0.41 s, inside the 0.5 s record),
     nt=500, dt=1 ms, 10 Hz Ricker, source at (500 m, 20 m), 101 surface
-    receivers, 4th order, r=4 Rademacher.  Gradient taken at homogeneous
-    1.5 km/s."""
+    receivers, 4th order, r=4 Rademacher, probe window T=128.  Gradient
+    taken at homogeneous 1.5 km/s."""
     nx = nz = 101
     nt, dt, f0 = 500, 1e-3, 10.0
     return Workload(
@@ -187,13 +187,14 @@ def config1(seed: int = DEFAULT_SEED) -> Workload:
         rec=surface_receivers_2d(nx).reshape(1, -1),
         vel_true=two_layer_2d(nz, nx, 1500.0, 2500.0, 25),
         vel0=np.full((nz, nx), 1500.0, np.float32),
-        wavelet=_wavelets(1, 1, nt, dt, f0), r=4, probe_kind="rademacher", seed=seed, T=32)
+        wavelet=_wavelets(1, 1, nt, dt, f0), r=4, probe_kind="rademacher", seed=seed, T=128)
 
 
 def config2(seed: int = DEFAULT_SEED, nt: int = 3000, nshots: int = 16) -> Workload:
     """2-D 601x201 at 12.5 m, gradient background 1.5-4.5 km/s + 5 % smooth
     random perturbation + elliptic lens, nt=3000, dt=1 ms, 8 Hz, 16 shots at
-    25 m depth, 601 surface receivers, 8th order, r=16 Gaussian probes."""
+    25 m depth, 601 surface receivers, 8th order, r=16 Gaussian probes,
+    probe window T=128."""
     nx, nz, h, dt, f0 = 601, 201, 12.5, 1e-3, 8.0
     vclip = 0.9 * CFL_LIMIT[(2, 8)] * h / dt
     xs = np.round(np.linspace(0, nx - 1, nshots + 2)[1:-1]).astype(np.int64)
@@ -204,7 +205,7 @@ def config2(seed: int = DEFAULT_SEED, nt: int = 3000, nshots: int = 16) -> Workl
         rec=np.broadcast_to(surface_receivers_2d(nx), (nshots, nx)).copy(),
         vel_true=gradient_lens_2d(nz, nx, seed, vclip=vclip),
         vel0=gradient_lens_2d(nz, nx, seed, vclip=vclip, background_only=True),
-        wavelet=_wavelets(nshots, 1, nt, dt, f0), r=16, probe_kind="gaussian", seed=seed, T=32)
+        wavelet=_wavelets(nshots, 1, nt, dt, f0), r=16, probe_kind="gaussian", seed=seed, T=128)
 
 
 def config3(seed: int = DEFAULT_SEED, n: int = 256, nt: int = 2000, T: int = 32,
@@ -226,7 +227,8 @@ def config3(seed: int = DEFAULT_SEED, n: int = 256, nt: int = 2000, T: int = 32,
 
 def config4(seed: int = DEFAULT_SEED, nt: int = 2500, nshots: int = 8) -> Workload:
     """Batch of 8 shots on 2-D 801x301 at 10 m, nt=2500, dt=1 ms, 8 Hz,
-    8th order, r=16 Gaussian probes, model generator of config 2."""
+    8th order, r=16 Gaussian probes, probe window T=128, model generator of
+    config 2."""
     nx, nz, h, dt, f0 = 801, 301, 10.0, 1e-3, 8.0
     vclip = 0.9 * CFL_LIMIT[(2, 8)] * h / dt
     xs = np.round(np.linspace(0, nx - 1, nshots + 2)[1:-1]).astype(np.int64)
@@ -237,7 +239,7 @@ def config4(seed: int = DEFAULT_SEED, nt: int = 2500, nshots: int = 8) -> Worklo
         rec=np.broadcast_to(surface_receivers_2d(nx), (nshots, nx)).copy(),
         vel_true=gradient_lens_2d(nz, nx, seed, vclip=vclip),
         vel0=gradient_lens_2d(nz, nx, seed, vclip=vclip, background_only=True),
-        wavelet=_wavelets(nshots, 1, nt, dt, f0), r=16, probe_kind="gaussian", seed=seed, T=32)
+        wavelet=_wavelets(nshots, 1, nt, dt, f0), r=16, probe_kind="gaussian", seed=seed, T=128)
 
 
 def small_2d(nx=67, nz=45, nt=160, order=8, nshots=1, r=4, probe_kind="rademacher",

@@ -48,7 +48,7 @@ def test_2d_batches(cfg, nx, nz, h, nt, nshots):
     w = getattr(wl, cfg)()
     _common(w)
     assert (w.ndim, w.nx, w.nz, w.h, w.nt, w.dt, w.f0, w.order) == (2, nx, nz, h, nt, 1e-3, 8.0, 8)
-    assert (w.nshots, w.r, w.probe_kind, w.T) == (nshots, 16, "gaussian", 32)
+    assert (w.nshots, w.r, w.probe_kind, w.T) == (nshots, 16, "gaussian", 128)
     assert w.rec.shape[1] == nx and np.all(_zyx(w, w.rec)[0] == 0)
     assert len(np.unique(w.src)) == nshots  # shots at distinct positions
     # smooth background 1.5 -> 4.5 km/s with depth; the true model adds perturbations and a lens
