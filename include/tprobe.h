@@ -321,7 +321,9 @@ typedef enum {
   TP_KERNEL_POINT = 3,    /* source injection + receiver sampling */
   TP_KERNEL_REDUCE = 4,   /* residual, misfit and norm reductions */
   TP_KERNEL_OTHER = 5,    /* setup kernels, probe generation, finish */
-  TP_KERNEL_KINDS = 6
+  TP_KERNEL_STEP_IMAGING = 6, /* 3-D adjoint step fused with the imaging
+                                 condition of the full-storage gradient */
+  TP_KERNEL_KINDS = 7
 } tp_kernel_kind;
 
 /* Starts recording a CUDA event pair around every kernel launch of the

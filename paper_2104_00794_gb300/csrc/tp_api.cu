@@ -4,10 +4,12 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "tp_internal.h"
@@ -485,9 +487,10 @@ tp_status forward_loop(const Ctx& c, const Fam& f, LevelFn level, const float* w
 // q_out (may be null) receives S lambda[t+1] at row t; acc/aval accumulate
 // sum_k lambda[k][src] q[k-1] for the full gradient's source term.  Without
 // acc, a 2-D batch runs on the cluster path as in forward_loop (levels form).
-template <class LevelFn, class AfterFn, class ClosesFn>
+// step_j (optional) replaces the plain step that forms level j.
+template <class LevelFn, class AfterFn, class ClosesFn, class StepFn = std::nullptr_t>
 tp_status adjoint_loop(const Ctx& c, const Fam& f, LevelFn level, const float* s, float* q_out, double* acc,
-                       const float* aval, AfterFn after_level, ClosesFn closes) {
+                       const float* aval, AfterFn after_level, ClosesFn closes, StepFn step_j = nullptr) {
   const Plan& P = c.P;
   const long long sss = (long long)P.nt * P.nrec, qss = (long long)P.nt * P.nsrc, ss = c.ss(f);
   const bool samp = q_out || acc;
@@ -511,7 +514,10 @@ tp_status adjoint_loop(const Ctx& c, const Fam& f, LevelFn level, const float* s
   if (P.form == TP_FORM_INCREMENT)  // lambda[nt] - lambda[nt+1] = 0
     TRY(cudaMemsetAsync(c.at<char>(P.o_w), 0, (size_t)P.nshots * P.L.field * sizeof(float), c.st));
   for (int j = P.nt - 1; j >= 2; --j) {
-    TRYS(step(c, f, level(j + 1), level(j + 2), level(j)));
+    if constexpr (std::is_same_v<StepFn, std::nullptr_t>)
+      TRYS(step(c, f, level(j + 1), level(j + 2), level(j)));
+    else
+      TRYS(step_j(j));
     TRYS(point(c, samp ? c.ptr(f, level(j + 1)) : nullptr, ss, c.at<long long>(P.o_soff), P.nsrc,
                q_out ? q_out + (long long)j * P.nsrc : nullptr, qss, c.ptr(f, level(j)), ss, c.at<long long>(P.o_roff),
                c.at<float>(P.o_cr), P.nrec, s + (long long)j * P.nrec, sss, acc,
@@ -925,12 +931,31 @@ tp_status tp_gradient_full(const tp_grid* grid, const tp_geom* geom, const float
   // adjoint with the imaging condition of Eq. 3 in its stencil form:
   // gacc_s += lambda_s[j] * S(u_s[j-1])   (udd[j] = v^2 (L u[j-1] + S^T q[j-1]))
   auto lam = [](int k) { return k % 3; };
-  auto imaging = [&](int j) -> tp_status {
-    StencilArgs a{c.ref(fh, j - 1), c.ref(fl, lam(j)), c.ref(fG, 0), c.ptr(fG, 0), c.ss(fG), P.nshots};
-    TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
-    return TP_OK;
-  };
-  TRYS(adjoint_loop(c, fl, lam, d, nullptr, c.at<double>(P.o_sacc), wavelet, imaging, [](int) { return true; }));
+  if (P.L.ndim == 3 && P.form == TP_FORM_LEVELS) {
+    // 3-D: in the sweep of the step that forms lambda[j], whose source field
+    // lambda[j+1] is complete: the terms j+1 = nt .. 3 in the same order and
+    // the same arithmetic as the separate sweep (lambda[nt] = 0 and u[1] = 0
+    // make the first and the omitted last term exactly zero)
+    const FieldRef c2 = c.ref(Fam{P.o_c2, 1, 0}, 0);
+    auto fused = [&](int j) -> tp_status {
+      StencilArgs a{c.ref(fl, lam(j + 1)), c.ref(fl, lam(j + 2)), c2, c.ptr(fl, lam(j)), c.ss(fl), P.nshots};
+      a.img = c.ref(fh, j);
+      a.gin = c.ref(fG, 0);
+      a.gout = c.ptr(fG, 0);
+      a.gout_ss = c.ss(fG);
+      TRY(launch_stencil(MODE_STEP_IMG, P.L, P.W, a, c.st, c.err()));
+      return TP_OK;
+    };
+    TRYS(adjoint_loop(c, fl, lam, d, nullptr, c.at<double>(P.o_sacc), wavelet, [](int) { return TP_OK; },
+                      [](int) { return true; }, fused));
+  } else {
+    auto imaging = [&](int j) -> tp_status {
+      StencilArgs a{c.ref(fh, j - 1), c.ref(fl, lam(j)), c.ref(fG, 0), c.ptr(fG, 0), c.ss(fG), P.nshots};
+      TRY(launch_stencil(MODE_IMAGE, P.L, P.W, a, c.st, c.err()));
+      return TP_OK;
+    };
+    TRYS(adjoint_loop(c, fl, lam, d, nullptr, c.at<double>(P.o_sacc), wavelet, imaging, [](int) { return true; }));
+  }
   TRY(launch_finish_grad(P.L, vel, c.at<float>(P.o_gacc), P.nshots, P.L.field, 1.0f / (grid->h * grid->h), grad,
                          c.st));
   TRY(launch_source_term(P.L, vel, geom->src, c.at<long long>(P.o_soff), P.nsrc, P.nshots, 1.0f, nullptr, nullptr, 0,
@@ -1006,7 +1031,8 @@ tp_status tp_profile_end(double* ms, int64_t* launches) {
 
 const char* tp_kernel_name(int kind) {
   static const char* names[TP_KERNEL_KINDS] = {"stencil_step", "imaging_sweep", "probe_gemm_tcgen05",
-                                               "point_inject_sample", "reduce_fp64", "setup_other"};
+                                               "point_inject_sample", "reduce_fp64", "setup_other",
+                                               "step_imaging_fused"};
   return (kind >= 0 && kind < TP_KERNEL_KINDS) ? names[kind] : "unknown";
 }
 

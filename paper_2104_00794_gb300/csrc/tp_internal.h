@@ -74,7 +74,7 @@ __host__ __device__ inline float sponge_a(const Layout& L, const Weights& W, lon
 Weights stencil_weights(int order);
 
 // ---------------------------------------------------------------- stencil
-enum StencilMode { MODE_STEP = 0, MODE_IMAGE = 1, MODE_INC = 2 };
+enum StencilMode { MODE_STEP = 0, MODE_IMAGE = 1, MODE_INC = 2, MODE_STEP_IMG = 3 };
 
 // A field of a "family": `nfields` consecutive padded fields starting at
 // `base` (a ring of levels, a history, the accumulators...).  Shot s uses
@@ -93,6 +93,9 @@ struct FieldRef {
 // MODE_INC  : w' = p1 + p2 * S(src), out = src + w', and w' is stored to out2
 //             (the increment form: p1 = out2 = the increment u[t] - u[t-1])
 // MODE_IMAGE: out = p2 + p1 * S(src)  (out may alias p2: accumulate)
+// MODE_STEP_IMG (3-D only): MODE_STEP, and in the same sweep
+//             gout = gin + src * S(img)  (the imaging condition of Eq. 3 on the
+//             step's own source field; gout may alias gin)
 // S(.) = the stencil sum without 1/h^2, in the centred form.  `out` is the shot-0 field,
 // out_ss the per-shot stride in floats.
 struct StencilArgs {
@@ -102,6 +105,10 @@ struct StencilArgs {
   int nshots;
   float* out2 = nullptr;     // MODE_INC: the increment field (same storage as p1)
   long long out2_ss = 0;
+  FieldRef img{};            // MODE_STEP_IMG: the field under the imaging stencil
+  FieldRef gin{};            // MODE_STEP_IMG: the accumulator read
+  float* gout = nullptr;     // MODE_STEP_IMG: the accumulator written (shot 0), per-shot stride gout_ss
+  long long gout_ss = 0;
 };
 cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& a,
                            cudaStream_t s, int* err);

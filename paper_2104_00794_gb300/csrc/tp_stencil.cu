@@ -195,7 +195,9 @@ cudaError_t launch_sweep3d_tma(int mode, const Layout& L, const Weights& W, cons
 // warp-strip kernel above.
 cudaError_t launch_stencil(int mode, const Layout& L, const Weights& W, const StencilArgs& sa,
                            cudaStream_t s, int* err) {
-  const int kind = mode == MODE_IMAGE ? 1 : 0;  // TP_KERNEL_IMAGING / TP_KERNEL_STENCIL
+  // TP_KERNEL_IMAGING / TP_KERNEL_STEP_IMAGING / TP_KERNEL_STENCIL
+  const int kind = mode == MODE_IMAGE ? 1 : (mode == MODE_STEP_IMG ? 6 : 0);
+  if (mode == MODE_STEP_IMG && L.ndim != 3) return cudaErrorInvalidValue;  // 3-D sweep only
   prof_before(kind, s);
   cudaError_t e;
   if (L.ndim == 3) {

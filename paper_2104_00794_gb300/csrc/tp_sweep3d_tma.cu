@@ -36,18 +36,27 @@ namespace {
 
 constexpr int NCONS = 256;                 // consumer threads, 4 x points each
 constexpr int NTHREADS = NCONS + 32;       // + one producer warp
+// lookahead of the fused step-and-imaging sweep, which runs one CTA per SM
+// (164 registers a thread at order 8; at two CTAs per SM the 96-register cap
+// spilled 1.7 KB a thread): full-storage gradient of 256^3, nt = 1000 on
+// GB300: 2 planes 326.9 ms, 3 planes 314.0 ms, 5 planes 311.7 ms
+constexpr int IMG_LA = 5;
 
-// Tile BX x BY (BX/4 * BY == NCONS) and LA planes of lookahead.
-template <int R, int BX_, int BY_, int LA_>
+// Tile BX x BY (BX/4 * BY == NCONS) and LA planes of lookahead.  IMG: the
+// fused step-and-imaging sweep, with a second haloed field (its planes share
+// the u stages' barriers) and the accumulator (sharing the u_old / c2 stages').
+template <int R, int BX_, int BY_, int LA_, bool IMG_ = false>
 struct Cfg {
   static constexpr int BX = BX_, BY = BY_, LA = LA_;
+  static constexpr bool IMG = IMG_;
   static_assert((BX / 4) * BY == NCONS, "one consumer thread per 4 points");
   static constexpr int NSU = R + 1 + LA;  // u stages
   static constexpr int NSP = LA + 1;      // u_old / c2 stages
+  static constexpr int NFU = IMG ? 2 : 1, NFP = IMG ? 3 : 2;  // fields per u stage, per u_old / c2 stage
   static constexpr int UW = BX + 8, UH = BY + 2 * R;
   static constexpr int UFL = UW * UH, PFL = BX * BY;
   static constexpr uint32_t UBYTES = UFL * 4, PBYTES = PFL * 4;
-  static constexpr size_t BAR_OFF = (size_t)(NSU * UFL + 2 * NSP * PFL) * 4;
+  static constexpr size_t BAR_OFF = (size_t)(NFU * NSU * UFL + NFP * NSP * PFL) * 4;
   static constexpr size_t SMEM = BAR_OFF + (size_t)(2 * NSU + 2 * NSP) * 8 + 16;
 };
 
@@ -55,6 +64,9 @@ struct TmaArgs {
   Layout L;
   Weights W;
   int f_src, fs_src, f_p1, fs_p1, f_p2, fs_p2;
+  int f_img, fs_img, f_g, fs_g;  // IMG: the imaged field and the accumulator read
+  float* gout;                   // IMG: the accumulator written
+  long long gout_ss;
   float* out;
   long long out_ss;
   float* out2;
@@ -153,17 +165,64 @@ __device__ __forceinline__ Seg segment(const TmaArgs& a, long long item) {
   return s;
 }
 
+// S of Eq. 1 at the 4 consecutive x points of one consumer thread: v gets the
+// centre row's 12 values around them (x - 4 .. x + 7), s4 the four sums.
+// Uc: the resident centre plane (x/y neighbours), q: the z queue (q[R] is the
+// centre plane's own float4).
+// Centred form: S(u) = sum_k w_k (sum of the 6 neighbours at distance k - 6u), the
+// -6u folded into one FMA per k (one rounding: fma(-6, u, sum), exact product).  It
+// equals w_0 * 3u + sum_k w_k (neighbours) for exact weights, but carries no w_0
+// term: with fp32-rounded weights the plain sum form keeps a spurious zero-order
+// term that makes long runs drift, while here a constant field leaves only the
+// rounding of its 6-fold sum, of either sign.  7 operations per k instead of the
+// 12 of the per-neighbour difference form (u[+k] - u) + (u[-k] - u), at the same
+// accuracy after thousands of steps.
+// Two points per instruction with the packed fp32x2 FMA / ADD: each lane is the
+// IEEE round-to-nearest operation of the scalar form, in the same order.
+template <int R, int RW>
+__device__ __forceinline__ void star4(const float4* Uc, const float4 (&q)[2 * R + 1], int cidx, const Weights& W,
+                                      float (&v)[12], float (&s4)[4]) {
+  const float4 xl = Uc[cidx - 1], xc = Uc[cidx], xr = Uc[cidx + 1];
+  v[0] = xl.x; v[1] = xl.y; v[2] = xl.z; v[3] = xl.w;
+  v[4] = xc.x; v[5] = xc.y; v[6] = xc.z; v[7] = xc.w;
+  v[8] = xr.x; v[9] = xr.y; v[10] = xr.z; v[11] = xr.w;
+  float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  const float2 m6 = make_float2(-6.f, -6.f);
+#pragma unroll
+  for (int k = 1; k <= R; ++k) {
+    const float4 yp = Uc[cidx + k * RW], ym = Uc[cidx - k * RW];
+    const float4 zp = q[R + k], zm = q[R - k];
+    const float2 wk = make_float2(W.w[k], W.w[k]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = 2 * h;
+      const float2 c = make_float2(v[4 + p], v[5 + p]);
+      const float2 xs = __fadd2_rn(make_float2(v[4 + p + k], v[5 + p + k]), make_float2(v[4 + p - k], v[5 + p - k]));
+      const float2 ys = __fadd2_rn(h ? make_float2(yp.z, yp.w) : make_float2(yp.x, yp.y),
+                                   h ? make_float2(ym.z, ym.w) : make_float2(ym.x, ym.y));
+      const float2 zs = __fadd2_rn(h ? make_float2(zp.z, zp.w) : make_float2(zp.x, zp.y),
+                                   h ? make_float2(zm.z, zm.w) : make_float2(zm.x, zm.y));
+      const float2 t = __ffma2_rn(m6, c, __fadd2_rn(__fadd2_rn(xs, ys), zs));
+      s2[h] = __ffma2_rn(wk, t, s2[h]);
+    }
+  }
+  s4[0] = s2[0].x; s4[1] = s2[0].y; s4[2] = s2[1].x; s4[3] = s2[1].y;
+}
+
 // DAMP: the grid has an absorbing layer (the undamped instantiation carries
 // no trace of it)
 template <int R, int MODE, class C, bool DAMP>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, C::SMEM + 1024 <= 114 * 1024 ? 2 : 1)
 sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mP1,
-            const __grid_constant__ CUtensorMap mP2, TmaArgs a) {
+            const __grid_constant__ CUtensorMap mP2, const __grid_constant__ CUtensorMap mI,
+            const __grid_constant__ CUtensorMap mG, TmaArgs a) {
   constexpr int BX = C::BX, BY = C::BY;
   extern __shared__ __align__(128) unsigned char smem[];
   float* sU = reinterpret_cast<float*>(smem);
-  float* sP1 = sU + C::NSU * C::UFL;
+  float* sI = sU + C::NSU * C::UFL;  // IMG only
+  float* sP1 = sU + C::NFU * C::NSU * C::UFL;
   float* sP2 = sP1 + C::NSP * C::PFL;
+  float* sG = sP2 + C::NSP * C::PFL;  // IMG only
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
   const uint32_t fullU = su32(bars), emptyU = fullU + 8 * C::NSU;
   const uint32_t fullP = emptyU + 8 * C::NSU, emptyP = fullP + 8 * C::NSP;
@@ -195,15 +254,18 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
       const int nzs = sg.z1 - sg.z0;
       if (nzs <= 0) continue;
       const int fu = a.f_src + sg.shot * a.fs_src, f1 = a.f_p1 + sg.shot * a.fs_p1, f2 = a.f_p2 + sg.shot * a.fs_p2;
+      const int fi = a.f_img + sg.shot * a.fs_img, fg = a.f_g + sg.shot * a.fs_g;
       for (int k = 0; k < nzs + 2 * R && ok; ++k) {
         const int su = ku % C::NSU;
         if (ku >= (uint32_t)C::NSU && !bar_wait(emptyU + 8 * su, ((ku / C::NSU) - 1) & 1, abort_flag, a.spin)) {
           ok = false;
           break;
         }
-        bar_expect_tx(fullU + 8 * su, C::UBYTES);
+        bar_expect_tx(fullU + 8 * su, C::NFU * C::UBYTES);
         // haloed u plane z = z0 - R + k: padded x from x0 - 4 + HX, y from y0 - R + H
         tma4(su32(sU + su * C::UFL), &mU, sg.x0 - 4 + HX, sg.y0 - R + H, sg.z0 - R + k + H, fu, fullU + 8 * su);
+        if (C::IMG)  // the imaged field's plane, same box
+          tma4(su32(sI + su * C::UFL), &mI, sg.x0 - 4 + HX, sg.y0 - R + H, sg.z0 - R + k + H, fi, fullU + 8 * su);
         ++ku;
         if (k >= 2 * R) {
           const int j = k - 2 * R;
@@ -212,9 +274,10 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
             ok = false;
             break;
           }
-          bar_expect_tx(fullP + 8 * sp, 2 * C::PBYTES);
+          bar_expect_tx(fullP + 8 * sp, C::NFP * C::PBYTES);
           tma4(su32(sP1 + sp * C::PFL), &mP1, sg.x0 + HX, sg.y0 + H, sg.z0 + j + H, f1, fullP + 8 * sp);
           tma4(su32(sP2 + sp * C::PFL), &mP2, sg.x0 + HX, sg.y0 + H, sg.z0 + j + H, f2, fullP + 8 * sp);
+          if (C::IMG) tma4(su32(sG + sp * C::PFL), &mG, sg.x0 + HX, sg.y0 + H, sg.z0 + j + H, fg, fullP + 8 * sp);
           ++kp;
         }
       }
@@ -242,6 +305,7 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
   const int tx = tid % (BX / 4), ty = tid / (BX / 4), lane = tid & 31;
   constexpr int RW = C::UW / 4;  // float4 per staged row
   const float4* U4 = reinterpret_cast<const float4*>(sU);
+  const float4* I4 = reinterpret_cast<const float4*>(sI);
   uint32_t ku = 0, kp = 0;
   bool ok = true;
   for (long long item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
@@ -251,14 +315,16 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
     const int x = sg.x0 + 4 * tx, y = sg.y0 + ty;
     float* out = a.out + sg.shot * a.out_ss;
     float* out2 = MODE == MODE_INC ? a.out2 + sg.shot * a.out2_ss : nullptr;
+    float* gout = C::IMG ? a.gout + sg.shot * a.gout_ss : nullptr;
     const int cidx = (ty + R) * RW + tx + 1;  // own float4 in a staged u plane
-    float4 q[2 * R + 1];
+    float4 q[2 * R + 1], qi[2 * R + 1];  // qi: the imaged field's z neighbours (IMG)
     // prologue: planes z0-R .. z0+R-1 fill the queue; the first R are released
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) {
       const uint32_t kk = ku + k, s = kk % C::NSU;
       if (!warp_wait(fullU + 8 * s, (kk / C::NSU) & 1, abort_flag, a.spin)) { ok = false; break; }
       q[k] = U4[s * (C::UFL / 4) + cidx];
+      if (C::IMG) qi[k] = I4[s * (C::UFL / 4) + cidx];
       if (k < R) {
         __syncwarp();
         if (lane == 0) bar_arrive(emptyU + 8 * s);
@@ -272,50 +338,21 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
       const uint32_t sc = kc % C::NSU, sn = kn % C::NSU, sp = kq % C::NSP;
       if (!warp_wait(fullU + 8 * sn, (kn / C::NSU) & 1, abort_flag, a.spin)) { ok = false; break; }
       q[2 * R] = U4[sn * (C::UFL / 4) + cidx];
+      if (C::IMG) qi[2 * R] = I4[sn * (C::UFL / 4) + cidx];
       if (!warp_wait(fullP + 8 * sp, (kq / C::NSP) & 1, abort_flag, a.spin)) { ok = false; break; }
-      const float4* Uc = U4 + sc * (C::UFL / 4);
-      const float4 xl = Uc[cidx - 1], xc = Uc[cidx], xr = Uc[cidx + 1];
-      const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-      // centred form: S(u) = sum_k w_k (sum of the 6 neighbours at distance k - 6u), the
-      // -6u folded into one FMA per k (one rounding: fma(-6, u, sum), exact product).  It
-      // equals w_0 * 3u + sum_k w_k (neighbours) for exact weights, but carries no w_0
-      // term: with fp32-rounded weights the plain sum form keeps a spurious zero-order
-      // term that makes long runs drift, while here a constant field leaves only the
-      // rounding of its 6-fold sum, of either sign.  7 operations per k instead of the
-      // 12 of the per-neighbour difference form (u[+k] - u) + (u[-k] - u), at the same
-      // accuracy after thousands of steps.
-      // Two points per instruction with the packed fp32x2 FMA / ADD: each lane is the
-      // IEEE round-to-nearest operation of the scalar form, in the same order.
-      float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-      const float2 m6 = make_float2(-6.f, -6.f);
-#pragma unroll
-      for (int k = 1; k <= R; ++k) {
-        const float4 yp = Uc[cidx + k * RW], ym = Uc[cidx - k * RW];
-        const float4 zp = q[R + k], zm = q[R - k];
-        const float2 wk = make_float2(a.W.w[k], a.W.w[k]);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int p = 2 * h;
-          const float2 c = make_float2(v[4 + p], v[5 + p]);
-          const float2 xs = __fadd2_rn(make_float2(v[4 + p + k], v[5 + p + k]), make_float2(v[4 + p - k], v[5 + p - k]));
-          const float2 ys = __fadd2_rn(h ? make_float2(yp.z, yp.w) : make_float2(yp.x, yp.y),
-                                       h ? make_float2(ym.z, ym.w) : make_float2(ym.x, ym.y));
-          const float2 zs = __fadd2_rn(h ? make_float2(zp.z, zp.w) : make_float2(zp.x, zp.y),
-                                       h ? make_float2(zm.z, zm.w) : make_float2(zm.x, zm.y));
-          const float2 t = __ffma2_rn(m6, c, __fadd2_rn(__fadd2_rn(xs, ys), zs));
-          s2[h] = __ffma2_rn(wk, t, s2[h]);
-        }
-      }
-      const float s4[4] = {s2[0].x, s2[0].y, s2[1].x, s2[1].y};
+      float v[12], s4[4], vi[12], si4[4];
+      star4<R, RW>(U4 + sc * (C::UFL / 4), q, cidx, a.W, v, s4);
+      if (C::IMG) star4<R, RW>(I4 + sc * (C::UFL / 4), qi, cidx, a.W, vi, si4);
       const float4 c1 = reinterpret_cast<const float4*>(sP1 + sp * C::PFL)[ty * (BX / 4) + tx];
       const float4 c2 = reinterpret_cast<const float4*>(sP2 + sp * C::PFL)[ty * (BX / 4) + tx];
-      float res[4], inc[4];
+      const float4 g4 = C::IMG ? reinterpret_cast<const float4*>(sG + sp * C::PFL)[ty * (BX / 4) + tx] : c1;
+      float res[4], inc[4], gnew[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const float c = v[4 + p];
         // damping of the absorbing layer (0 outside it: the undamped expressions)
         const float ad = (DAMP && MODE != MODE_IMAGE) ? sponge_a(a.L, a.W, sg.z0 + j, y, x + p) : 0.f;
-        if (MODE == MODE_STEP) {
+        if (MODE == MODE_STEP || MODE == MODE_STEP_IMG) {
           res[p] = ad == 0.f ? fmaf(comp(c2, p), s4[p], 2.0f * c - comp(c1, p))
                              : fmaf(comp(c2, p), s4[p], 2.0f * c - (1.0f - ad) * comp(c1, p)) / (1.0f + ad);
         } else if (MODE == MODE_INC) {
@@ -325,6 +362,8 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
         } else {
           res[p] = fmaf(comp(c1, p), s4[p], comp(c2, p));
         }
+        // imaging: the step's own source field (centre) times S of the imaged field
+        if (C::IMG) gnew[p] = fmaf(c, si4[p], comp(g4, p));
       }
       __syncwarp();
       if (lane == 0) {
@@ -336,17 +375,22 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
         if (x + 3 < a.L.nx) {
           *reinterpret_cast<float4*>(out + o) = make_float4(res[0], res[1], res[2], res[3]);
           if (MODE == MODE_INC) *reinterpret_cast<float4*>(out2 + o) = make_float4(inc[0], inc[1], inc[2], inc[3]);
+          if (C::IMG) *reinterpret_cast<float4*>(gout + o) = make_float4(gnew[0], gnew[1], gnew[2], gnew[3]);
         } else {
 #pragma unroll
           for (int p = 0; p < 4; ++p)
             if (x + p < a.L.nx) {
               out[o + p] = res[p];
               if (MODE == MODE_INC) out2[o + p] = inc[p];
+              if (C::IMG) gout[o + p] = gnew[p];
             }
         }
       }
 #pragma unroll
-      for (int k = 0; k < 2 * R; ++k) q[k] = q[k + 1];
+      for (int k = 0; k < 2 * R; ++k) {
+        q[k] = q[k + 1];
+        if (C::IMG) qi[k] = qi[k + 1];
+      }
     }
     if (!ok) break;
     // the last R planes were only queue heads: release them
@@ -430,20 +474,27 @@ bool encode_field_map(const Layout& L, const void* base, long long nfields, int 
 namespace {
 
 template <int R, int MODE, class C, bool DAMP>
-cudaError_t launch_k(const CUtensorMap& mU, const CUtensorMap& m1, const CUtensorMap& m2, const TmaArgs& t,
-                     long long blocks, cudaStream_t s) {
+cudaError_t launch_k(const CUtensorMap& mU, const CUtensorMap& m1, const CUtensorMap& m2, const CUtensorMap& mI,
+                     const CUtensorMap& mG, const TmaArgs& t, long long blocks, cudaStream_t s) {
   const cudaError_t e = smem_limit_once<sweep3d_tma<R, MODE, C, DAMP>>((int)C::SMEM);
   if (e != cudaSuccess) return e;
-  sweep3d_tma<R, MODE, C, DAMP><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, t);
+  sweep3d_tma<R, MODE, C, DAMP><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, mI, mG, t);
   return cudaGetLastError();
 }
 
 template <int R, int MODE, class C>
 cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
   constexpr int BX = C::BX, BY = C::BY;
-  CUtensorMap mU, m1, m2;
+  CUtensorMap mU, m1, m2, mI, mG;
   if (!get_map(L, a.src, C::UW, C::UH, &mU) || !get_map(L, a.p1, BX, BY, &m1) || !get_map(L, a.p2, BX, BY, &m2))
     return cudaErrorInvalidValue;
+  if (C::IMG) {
+    if (!a.gout || !get_map(L, a.img, C::UW, C::UH, &mI) || !get_map(L, a.gin, BX, BY, &mG))
+      return cudaErrorInvalidValue;
+  } else {
+    mI = mU;  // unused
+    mG = m1;
+  }
   TmaArgs t;
   t.L = L;
   t.W = W;
@@ -454,6 +505,10 @@ cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cu
   t.out_ss = a.out_ss;
   t.out2 = a.out2;
   t.out2_ss = a.out2_ss;
+  t.f_img = a.img.f0; t.fs_img = a.img.fs;
+  t.f_g = a.gin.f0; t.fs_g = a.gin.fs;
+  t.gout = a.gout;
+  t.gout_ss = a.gout_ss;
   t.nshots = a.nshots;
   t.ntx = (L.nx + BX - 1) / BX;
   t.nty = (L.ny + BY - 1) / BY;
@@ -481,8 +536,8 @@ cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cu
   t.nzc = (L.nz + t.zchunk - 1) / t.zchunk;
   t.items = cols * t.nzc;
   const long long blocks = std::min<long long>(t.items, slots);
-  if (MODE != MODE_IMAGE && W.sw > 0) return launch_k<R, MODE, C, true>(mU, m1, m2, t, blocks, s);
-  return launch_k<R, MODE, C, false>(mU, m1, m2, t, blocks, s);
+  if (MODE != MODE_IMAGE && W.sw > 0) return launch_k<R, MODE, C, true>(mU, m1, m2, mI, mG, t, blocks, s);
+  return launch_k<R, MODE, C, false>(mU, m1, m2, mI, mG, t, blocks, s);
 }
 
 // 64 x 16 tiles, 3 planes of lookahead: 128 x 8, 32 x 32 tiles measured the
@@ -491,7 +546,8 @@ cudaError_t launch_c(const Layout& L, const Weights& W, const StencilArgs& a, cu
 // the copy pipeline, sets the pace.
 template <int R, int MODE>
 cudaError_t launch_t(const Layout& L, const Weights& W, const StencilArgs& a, cudaStream_t s, int* err) {
-  return launch_c<R, MODE, Cfg<R, 64, 16, 3>>(L, W, a, s, err);
+  if constexpr (MODE == MODE_STEP_IMG) return launch_c<R, MODE, Cfg<R, 64, 16, IMG_LA, true>>(L, W, a, s, err);
+  else return launch_c<R, MODE, Cfg<R, 64, 16, 3>>(L, W, a, s, err);
 }
 
 }  // namespace
@@ -501,10 +557,12 @@ cudaError_t launch_sweep3d_tma(int mode, const Layout& L, const Weights& W, cons
   if (W.R == 4) {
     if (mode == MODE_STEP) return launch_t<4, MODE_STEP>(L, W, a, s, err);
     if (mode == MODE_INC) return launch_t<4, MODE_INC>(L, W, a, s, err);
+    if (mode == MODE_STEP_IMG) return launch_t<4, MODE_STEP_IMG>(L, W, a, s, err);
     return launch_t<4, MODE_IMAGE>(L, W, a, s, err);
   }
   if (mode == MODE_STEP) return launch_t<2, MODE_STEP>(L, W, a, s, err);
   if (mode == MODE_INC) return launch_t<2, MODE_INC>(L, W, a, s, err);
+  if (mode == MODE_STEP_IMG) return launch_t<2, MODE_STEP_IMG>(L, W, a, s, err);
   return launch_t<2, MODE_IMAGE>(L, W, a, s, err);
 }
 

@@ -23,7 +23,7 @@ OP_FORWARD, OP_ADJOINT, OP_GRADIENT_PROBED, OP_GRADIENT_FULL, OP_PROBED_FORWARD,
 ACC_TYPES = {"f32": 0, "bf16": 1, "bf16_kahan": 2, "f32_fold": 3}
 IMAGE_CONDS = {"correlation": 0, "gradient": 1}
 TIME_FORMS = {"levels": 0, "increment": 1, "compensated": 2}
-KERNEL_KINDS = 6
+KERNEL_KINDS = 7
 
 
 class tp_grid(ctypes.Structure):
