@@ -38,7 +38,7 @@ constexpr int NCONS = 256;                 // consumer threads, 4 x points each
 constexpr int NTHREADS = NCONS + 32;       // + one producer warp
 // lookahead of the fused step-and-imaging sweep, which runs one CTA per SM
 // (164 registers a thread at order 8; at two CTAs per SM the 96-register cap
-// spilled 1.7 KB a thread): full-storage gradient of 256^3, nt = 1000 on
+// spilled 1.7 KB a thread): full-storage gradient of 256^3, nt = 2000 on
 // GB300: 2 planes 326.9 ms, 3 planes 314.0 ms, 5 planes 311.7 ms
 constexpr int IMG_LA = 5;
 
