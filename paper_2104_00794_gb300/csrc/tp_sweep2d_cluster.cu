@@ -63,6 +63,7 @@ struct C2Args {
   Layout L;
   Weights W;
   int nshots, C, rpc, sx, nx4;
+  int capi, caps;  // capacities of a band's injection and sampling lists (entries)
   int comp, dir, lev0, nsteps, fresh;
   float* ring; int nslots; long long ring_ss;  // level l of shot s: ring + s*ring_ss + (l % nslots)*L.field
   __nv_bfloat16* eslots; long long e_ss;       // comp: e of level l: eslots + s*e_ss + (l % 2)*L.field
@@ -160,11 +161,11 @@ __global__ void __launch_bounds__(C2_THREADS, 1) sweep2d_cluster(C2Args a) {
   const float** rowU = reinterpret_cast<const float**>(p);  // [2][nrt]: rows z0 - R .. z0 + rpc + R - 1
   const __nv_bfloat16** rowE = reinterpret_cast<const __nv_bfloat16**>(rowU + 2 * nrt);
   int* iloc = reinterpret_cast<int*>(rowE + 2 * nrt);  // injection: node (band index)
-  int* imeta = iloc + C2_MAXLIST;                       // k | leader << 16 | (next + 1) << 17
-  float* ival = reinterpret_cast<float*>(imeta + C2_MAXLIST);
-  int* sloc = reinterpret_cast<int*>(ival + C2_MAXLIST);  // sampling: node, column
-  int* sk = sloc + C2_MAXLIST;
-  int* cnt = sk + C2_MAXLIST;  // [0] injection, [1] sampling entries, [4 ..] per-warp counts
+  int* imeta = iloc + a.capi;                           // k | leader << 16 | (next + 1) << 17
+  float* ival = reinterpret_cast<float*>(imeta + a.capi);
+  int* sloc = reinterpret_cast<int*>(ival + a.capi);    // sampling: node, column
+  int* sk = sloc + a.caps;
+  int* cnt = sk + a.caps;  // [0] injection, [1] sampling entries, [4 ..] per-warp counts
 
   for (int i = tid; i < 2 * nrt; i += C2_THREADS) {
     const int b = i / nrt, zz = z0 - R + i % nrt;
@@ -521,21 +522,24 @@ __global__ void __launch_bounds__(C2_THREADS, 1) sweep2d_cluster(C2Args a) {
   }
 }
 
-size_t c2_smem(int rpc, int sx, int R, bool comp) {
+// list capacity for n entries (a band may hold all of a shot's entries)
+int c2_cap(int n) { return (std::max(n, 1) + 3) / 4 * 4; }
+
+size_t c2_smem(int rpc, int sx, int R, bool comp, int capi, int caps) {
   size_t b = (size_t)(2 * rpc + 1) * sx * 4;                // both levels, zero row
   if (comp) b += (size_t)2 * rpc * sx * 2;                  // low parts of both levels (bf16)
   b += (size_t)2 * 2 * (rpc + 2 * R) * sizeof(void*);       // row tables
-  b += (size_t)C2_MAXLIST * (3 * 4 + 2 * 4);                // injection and sampling entries
+  b += (size_t)capi * 3 * 4 + (size_t)caps * 2 * 4;         // injection and sampling entries
   b += (size_t)(4 + C2_THREADS / 32) * 4;                   // counts
   return (b + 15) / 16 * 16;
 }
 
 // the sizes a band of rpc rows of this grid needs; 0 if it does not fit
-size_t c2_fit(const Layout& L, int R, int C, bool comp, int* rpc_out) {
+size_t c2_fit(const Layout& L, int R, int C, bool comp, int capi, int caps, int* rpc_out) {
   const int nx4 = (L.nx + 3) / 4, sx = 4 * nx4 + 8;
   const int rpc = (L.nz + C - 1) / C;
   if (nx4 > C2_MAXCOL) return 0;
-  const size_t sm = c2_smem(rpc, sx, R, comp);
+  const size_t sm = c2_smem(rpc, sx, R, comp, capi, caps);
   if (sm > 227 * 1024) return 0;
   *rpc_out = rpc;
   return sm;
@@ -585,12 +589,12 @@ int c2_max_clusters(int C, size_t smem) {
 // batch's clusters need on this device (a CTA below ~1024 items counts as
 // 1024: more CTAs then only add barrier participants).
 template <int R, bool COMP>
-C2Plan c2_plan(const Layout& L, int nshots) {
+C2Plan c2_plan(const Layout& L, int nshots, int capi, int caps) {
   C2Plan best;
   long long best_est = -1;
   for (int C = 1; C <= C2_MAXC; ++C) {
     int rpc = 0;
-    const size_t sm = c2_fit(L, R, C, COMP, &rpc);
+    const size_t sm = c2_fit(L, R, C, COMP, capi, caps, &rpc);
     if (!sm) continue;
     const int ncl = c2_max_clusters<R, COMP>(C, sm);
     if (ncl < 1) continue;
@@ -614,7 +618,8 @@ cudaError_t c2_launch(const C2Args& a0, cudaStream_t s) {
   auto kern = sweep2d_cluster<R, COMP>;
   cudaError_t e = smem_limit_once<sweep2d_cluster<R, COMP>>(227 * 1024, true);
   if (e != cudaSuccess) return e;
-  const C2Plan pl = c2_plan<R, COMP>(a0.L, a0.nshots);
+  const int capi = c2_cap(a0.ninj), caps = c2_cap(a0.nsamp);
+  const C2Plan pl = c2_plan<R, COMP>(a0.L, a0.nshots, capi, caps);
   if (!pl.C) return cudaErrorInvalidConfiguration;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -633,6 +638,8 @@ cudaError_t c2_launch(const C2Args& a0, cudaStream_t s) {
   a.rpc = pl.rpc;
   a.sx = pl.sx;
   a.nx4 = pl.nx4;
+  a.capi = capi;
+  a.caps = caps;
   e = cudaLaunchKernelEx(&cfg, kern, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -644,9 +651,11 @@ bool cluster2d_fits(const Layout& L, const Weights& W, int nshots, int nsrc, int
   (void)nshots;
   if (L.ndim != 2 || W.sw > 0) return false;
   if (nsrc > C2_MAXLIST || nrec > C2_MAXLIST) return false;
+  // the larger of the two sets in both lists covers the forward and the adjoint launches
+  const int cap = c2_cap(std::max(nsrc, nrec));
   int rpc = 0;
   for (int C = 1; C <= C2_MAXC; ++C)
-    if (c2_fit(L, W.R, C, comp, &rpc)) return true;
+    if (c2_fit(L, W.R, C, comp, cap, cap, &rpc)) return true;
   return false;
 }
 
