@@ -34,8 +34,6 @@ namespace tp {
 
 namespace {
 
-constexpr int NCONS = 256;                 // consumer threads, 4 x points each
-constexpr int NTHREADS = NCONS + 32;       // + one producer warp
 // lookahead of the fused step-and-imaging sweep, which runs one CTA per SM
 // (164 registers a thread at order 8; at two CTAs per SM the 96-register cap
 // spilled 1.7 KB a thread): full-storage gradient of 256^3, nt = 2000 on
@@ -49,7 +47,9 @@ template <int R, int BX_, int BY_, int LA_, bool IMG_ = false>
 struct Cfg {
   static constexpr int BX = BX_, BY = BY_, LA = LA_;
   static constexpr bool IMG = IMG_;
-  static_assert((BX / 4) * BY == NCONS, "one consumer thread per 4 points");
+  static constexpr int NCONS = (BX / 4) * BY;  // consumer threads, 4 x points each
+  static constexpr int NTHREADS = NCONS + 32;  // + one producer warp
+  static_assert(NCONS % 32 == 0 && NCONS <= 992, "whole consumer warps");
   static constexpr int NSU = R + 1 + LA;  // u stages
   static constexpr int NSP = LA + 1;      // u_old / c2 stages
   static constexpr int NFU = IMG ? 2 : 1, NFP = IMG ? 3 : 2;  // fields per u stage, per u_old / c2 stage
@@ -212,7 +212,7 @@ __device__ __forceinline__ void star4(const float4* Uc, const float4 (&q)[2 * R 
 // DAMP: the grid has an absorbing layer (the undamped instantiation carries
 // no trace of it)
 template <int R, int MODE, class C, bool DAMP>
-__global__ void __launch_bounds__(NTHREADS, C::SMEM + 1024 <= 114 * 1024 ? 2 : 1)
+__global__ void __launch_bounds__(C::NTHREADS, C::SMEM + 1024 <= 114 * 1024 ? 2 : 1)
 sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mP1,
             const __grid_constant__ CUtensorMap mP2, const __grid_constant__ CUtensorMap mI,
             const __grid_constant__ CUtensorMap mG, TmaArgs a) {
@@ -232,11 +232,11 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
   if (tid == 0) {
     for (int s = 0; s < C::NSU; ++s) {
       bar_init(fullU + 8 * s, 1);
-      bar_init(emptyU + 8 * s, NCONS / 32);
+      bar_init(emptyU + 8 * s, C::NCONS / 32);
     }
     for (int s = 0; s < C::NSP; ++s) {
       bar_init(fullP + 8 * s, 1);
-      bar_init(emptyP + 8 * s, NCONS / 32);
+      bar_init(emptyP + 8 * s, C::NCONS / 32);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -244,9 +244,9 @@ sweep3d_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUte
   __syncthreads();
 
 
-  if (tid >= NCONS) {
+  if (tid >= C::NCONS) {
     // ------------------------------------------------------------ producer
-    if (tid != NCONS) return;
+    if (tid != C::NCONS) return;
     uint32_t ku = 0, kp = 0;
     bool ok = true;
     for (long long item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
@@ -478,7 +478,7 @@ cudaError_t launch_k(const CUtensorMap& mU, const CUtensorMap& m1, const CUtenso
                      const CUtensorMap& mG, const TmaArgs& t, long long blocks, cudaStream_t s) {
   const cudaError_t e = smem_limit_once<sweep3d_tma<R, MODE, C, DAMP>>((int)C::SMEM);
   if (e != cudaSuccess) return e;
-  sweep3d_tma<R, MODE, C, DAMP><<<(unsigned)blocks, NTHREADS, C::SMEM, s>>>(mU, m1, m2, mI, mG, t);
+  sweep3d_tma<R, MODE, C, DAMP><<<(unsigned)blocks, C::NTHREADS, C::SMEM, s>>>(mU, m1, m2, mI, mG, t);
   return cudaGetLastError();
 }
 
