@@ -322,6 +322,45 @@ def test_config_2_4_shot_subset_full_nt(cfg):
     assert err < err_levels
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("cfg", ["config2", "config4"])
+def test_config_2_4_every_shot_full_nt(cfg):
+    """All 16 (config 2) and 8 (config 4) shots at the full time axis, in the
+    batched launch the bench times: every shot's traces against the oracle;
+    and, since batched shots are independent, the batch's probed gradient and
+    misfit against the sums over the shots computed one shot per call (each
+    with the batch's probes of that shot, passed as user probes).  The
+    two-shot test above pins the gradient itself to the oracle."""
+    w = getattr(wl, cfg)()
+    p = api.Problem.from_workload(w)
+    vel, wav = to_dev(w.vel0), to_dev(w.wavelet)
+    d = host(p.forward(vel, wav))
+    ref = oracle.batch_forward(w, w.vel0)
+    errs = [rel_l2(d[s], ref[s]) for s in range(w.nshots)]
+    print(f"{cfg}: worst shot's traces {max(errs):.3e}")
+    assert max(errs) <= TRACE_TOL, errs
+    dobs = to_dev(oracle_dobs(w))
+    spec = api.ProbeSpec(kind="gaussian", r=16, T=32, seed=w.seed)
+    gb, sb = p.gradient_probed(vel, wav, dobs, spec)
+    gb, sb = host(gb).astype(np.float64), host(sb)
+    p.release()
+    gsum, jsum = np.zeros_like(gb), 0.0
+    for s in range(w.nshots):
+        ws = dataclasses.replace(w, nshots=1, src=w.src[s:s + 1], rec=w.rec[s:s + 1],
+                                 wavelet=np.ascontiguousarray(w.wavelet[s:s + 1]))
+        ps = api.Problem.from_workload(ws)
+        Z = p.probes(spec, s)[None].contiguous()
+        user = api.ProbeSpec(kind="user", r=16, T=32, Z_user=Z, scale=1.0 / 16)
+        g, sc = ps.gradient_probed(vel, wav[s:s + 1].contiguous(), dobs[s:s + 1].contiguous(), user)
+        gsum += host(g).astype(np.float64)
+        jsum += float(host(sc)[0])
+        ps.release()
+    err = rel_l2(gb, gsum)
+    print(f"{cfg}: batch gradient against the sum of {w.nshots} single-shot gradients {err:.3e}")
+    assert err <= 2e-6, err
+    assert sb[0] == pytest.approx(jsum, rel=1e-9)
+
+
 @pytest.mark.parametrize("sponge", [0, 6], ids=["rigid", "sponge"])
 def test_coincident_points_per_step_path_deterministic(sponge):
     """3-D (and a 2-D grid with an absorbing layer): the per-step path.  Two
