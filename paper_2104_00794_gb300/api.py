@@ -252,7 +252,9 @@ class Problem:
 
     @_on_device
     def status(self, op: int):
-        """Raises if a bounded device-side wait of the last `op` call timed out."""
+        """Raises the device-side errors of the last `op` call (and clears them): a bounded wait
+        that timed out (TP_ERR_TIMEOUT), a source or receiver index outside the grid when the
+        call ran without a host check (vmax given; TP_ERR_ARG), rank-deficient QR probes."""
         buf = self._ws.get(op)
         if buf is None:
             return

@@ -241,6 +241,19 @@ def test_errors_are_reported():
         bad = api.Problem(2, w.nx, 1, w.nz, w.h, w.dt, w.nt, w.order, w.src, np.array([[0, w.N + 5]]))
         bad.forward(vel, to_dev(w.wavelet))
     assert e.value.status == native.TP_ERR_ARG
+    # with vmax given the call does not synchronise: the kernels skip the bad entry (its trace
+    # is zero), the valid one is sampled as usual, and the status read reports the index
+    vmax = float(w.vel0.max())
+    bad = api.Problem(2, w.nx, 1, w.nz, w.h, w.dt, w.nt, w.order, w.src, np.array([[int(w.rec[0, 3]), w.N + 5]]),
+                      vmax=vmax)
+    d = host(bad.forward(vel, to_dev(w.wavelet)))
+    with pytest.raises(native.TprobeError) as e:
+        bad.status(native.OP_FORWARD)
+    assert e.value.status == native.TP_ERR_ARG
+    assert not d[0, :, 1].any()
+    good = api.Problem(2, w.nx, 1, w.nz, w.h, w.dt, w.nt, w.order, w.src, w.rec[:, 3:4], vmax=vmax)
+    assert np.array_equal(d[0, :, 0], host(good.forward(vel, to_dev(w.wavelet)))[0, :, 0])
+    bad.status(native.OP_FORWARD)  # the read cleared the flag
     with pytest.raises(native.TprobeError) as e:   # workspace too small
         native.tp_forward(p.grid, p.geom, vel.data_ptr(), vel.data_ptr(), vel.data_ptr(), vel.data_ptr(), 256,
                           torch.cuda.current_stream().cuda_stream)
