@@ -20,6 +20,11 @@
 //     live in a register queue of 2R+1 float4, x/y neighbours are read from
 //     the resident centre plane (x halo from the box, zero halo layers from
 //     the padded layout), so every value crosses HBM about once per step;
+//   * the full-storage adjoint (MODE_STEP_IMG) also stages the history level
+//     u[j] (haloed, on the u stages' barriers) and the gradient accumulator (on
+//     the u_old / c2 stages'), keeps u[j]'s z neighbours in a second register
+//     queue, and adds the imaging term of Eq. 3, lambda[j+1] * S(u[j]), in the
+//     same pass: 28 B per point instead of 16 + 16 in two sweeps, one CTA per SM;
 //   * every wait is bounded (clock64); on a timeout the CTA sets bit 0 of
 //     *err, stops issuing, drains its own copies (bounded) and exits.
 #include <cuda.h>
