@@ -44,3 +44,24 @@ def test_committed_profiles_parse():
         for field in ("dram_bytes_per_launch_full_size", "source_sha256", "applies_to", "ncu "):
             assert field in text, (f, field)
         assert "--clock-control none" in text
+
+
+def test_every_profile_gives_its_ncu_command():
+    """Each summary under profiles/ states the ncu command that made it, with
+    the clocks left alone (--clock-control none on every ncu line)."""
+    root = os.path.join(os.path.dirname(os.path.abspath(bench.__file__)), "profiles")
+    names = sorted(f for f in os.listdir(root) if f.endswith(".md"))
+    assert len(names) >= 5
+    for f in names:
+        lines = open(os.path.join(root, f)).read().splitlines()
+        cmds, cur = [], None  # commands with their backslash-continued lines joined
+        for ln in lines:
+            if cur is None and ln.lstrip().startswith("ncu "):
+                cur = ""
+            if cur is not None:
+                cur += " " + ln.rstrip().rstrip("\\")
+                if not ln.rstrip().endswith("\\"):
+                    cmds.append(cur)
+                    cur = None
+        assert cmds, f
+        assert all("--clock-control none" in c for c in cmds), f
